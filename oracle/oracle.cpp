@@ -1,0 +1,397 @@
+// oracle.cpp -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.
+//
+// A plain, slow, single-purpose CPU restatement of the PilotANN top-k search
+// (Gui et al., "PilotANN: Memory-Bounded GPU Acceleration for Vector Search",
+// arxiv 2503.21206).  Only the tests, the smoke check and the benchmark's CPU
+// baseline leg may load this library; the product search path never does.
+//
+// Arithmetic: every inner product / squared difference is accumulated in
+// FP64 over the stored inputs (FP32 rows, or BF16 / FP8-E4M3 rows decoded
+// exactly), and each finished distance (and each projected query component)
+// is rounded ONCE to FP32, the precision the paper fixes for all distance
+// calculations (Sec. 6.1, "Experimental Setup").  Every ordering decision is
+// taken on those FP32 values with ties broken by the original node id.
+//
+// No blocking, fusion or reordering: loops follow the definitions in the
+// paper's order.  Nothing here is shared with the GPU path.
+//
+// Parity pins (tests/test_oracle_pins.py): orthonormal basis, projection
+// with d'=d equals the full distance, projected <= full distance (Sec. 4.1),
+// brute-force limit (subgraph = full graph, d'=d, ef >= N), hand-computed
+// Algorithm 1 traces (tests/golden/), dense FES == argmin over the entry set
+// (Table 2, "FES (1 block)"), graceful degradation (Sec. 4.1 "Summary").
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- inputs --
+
+struct Index {
+    int64_t n, d, dp, R, R_sub, n_entry;
+    int metric;                     // 0: squared L2, 1: inner product (-<q,x>)
+    const int32_t* graph;           // n x R, original ids, -1 padded
+    const uint8_t* subgraph_mask;   // n, 1 = sampled (Sec. 4.3)
+    const int32_t* subgraph;        // n x R_sub, original ids, -1 padded; rows of unsampled nodes unused
+    const double* basis;            // d x dp, basis[j*dp + c] = V[j][c] (right singular vectors)
+    const void* reduced;            // n_sub x dp, rows of sampled nodes in ascending original id order
+    int reduced_dtype;              // 0: FP32, 1: BF16, 2: FP8 E4M3 (fn) with per-row FP32 scale
+    const float* reduced_scales;    // n_sub (FP8 only)
+    const float* full;              // n x d FP32 original vectors
+    const int32_t* entry_ids;       // n_entry original ids (all sampled)
+};
+
+struct Params {
+    int k, ef;
+    int stage1;              // 1: run stage (1) on the subgraph (Sec. 4.1)
+    int stage2_expansions;   // expansions of stage (2) on the subgraph (paper: 2)
+    int stage3;              // 1: run stage (3) on the full graph
+    int use_fes;             // 1: dense FES over the entry set; 0: entry = entry_ids[0]
+    int nthreads;
+};
+
+// Per-query outputs.  Any pointer may be null.
+struct Outputs {
+    int32_t* ids;        // nq x k, original ids, -1 padded
+    float* dists;        // nq x k, +inf padded
+    int32_t* counters;   // nq x 8: exp1, dist1, exp2, dist2, exp3, dist3, rerank, entry
+    int32_t* pool1_ids;  // nq x ef: C after stage (1), original ids
+    float* pool1_dists;  // nq x ef: reduced-space FP32 distances
+    int32_t* pool2_ids;  // nq x ef: C after re-rank + stage (2)
+    float* pool2_dists;  // nq x ef: full-vector FP32 distances
+};
+
+// ------------------------------------------------------- number formats --
+
+// BF16 -> FP64: a BF16 value is the upper 16 bits of an IEEE binary32.
+double decode_bf16(uint16_t h) {
+    uint32_t bits = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return double(f);
+}
+
+// FP8 E4M3 "fn" -> FP64 from the format definition: 1 sign bit, 4 exponent
+// bits (bias 7), 3 mantissa bits, subnormals when the exponent field is 0,
+// and S.1111.111 the only NaN (no infinities).
+double decode_e4m3(uint8_t c) {
+    int sign = (c >> 7) & 1;
+    int e = (c >> 3) & 0xF;
+    int m = c & 7;
+    double v;
+    if (e == 0xF && m == 7) return NAN;
+    if (e == 0) v = std::ldexp(double(m) / 8.0, 1 - 7);
+    else v = std::ldexp(1.0 + double(m) / 8.0, e - 7);
+    return sign ? -v : v;
+}
+
+// ------------------------------------------------------------ distances --
+
+// Exact-then-round: the FP64 value of the distance, rounded once to FP32.
+// Squared Euclidean for metric 0 (Sec. 5, Table 2 "squared euclidean");
+// negated inner product for metric 1 so that smaller is closer.
+float finish(double s, int metric) {
+    float f = float(metric == 0 ? s : -s);
+    if (f == 0.0f) f = 0.0f;  // -0.0 compares as +0.0
+    return f;
+}
+
+double accumulate(const double* q, const double* x, int64_t d, int metric) {
+    double s = 0.0;
+    for (int64_t i = 0; i < d; ++i) {
+        if (metric == 0) {
+            double t = q[i] - x[i];
+            s += t * t;
+        } else {
+            s += q[i] * x[i];
+        }
+    }
+    return s;
+}
+
+struct Cand {
+    float dist;
+    int32_t id;      // original node id
+    bool checked;
+};
+
+bool cand_less(const Cand& a, const Cand& b) {
+    if (a.dist != b.dist) return a.dist < b.dist;
+    return a.id < b.id;
+}
+
+struct Counters {
+    int32_t exp = 0, dist = 0;
+};
+
+// One query's view of the index.
+struct Searcher {
+    const Index& ix;
+    std::vector<int64_t> reduced_row;   // original id -> reduced row (-1 if unsampled)
+
+    explicit Searcher(const Index& index) : ix(index), reduced_row(index.n, -1) {
+        int64_t r = 0;
+        for (int64_t v = 0; v < ix.n; ++v)
+            if (ix.subgraph_mask[v]) reduced_row[v] = r++;
+    }
+
+    // Decoded reduced row of original node v (x_primary, Sec. 4.1 (1)).
+    void reduced_vec(int32_t v, double* out) const {
+        int64_t r = reduced_row[v];
+        for (int64_t c = 0; c < ix.dp; ++c) {
+            int64_t at = r * ix.dp + c;
+            if (ix.reduced_dtype == 0) out[c] = double(((const float*)ix.reduced)[at]);
+            else if (ix.reduced_dtype == 1) out[c] = decode_bf16(((const uint16_t*)ix.reduced)[at]);
+            else out[c] = decode_e4m3(((const uint8_t*)ix.reduced)[at]) * double(ix.reduced_scales[r]);
+        }
+    }
+
+    float reduced_dist(const double* qp, int32_t v, double* tmp) const {
+        reduced_vec(v, tmp);
+        return finish(accumulate(qp, tmp, ix.dp, ix.metric), ix.metric);
+    }
+
+    float full_dist(const double* q, int32_t v, double* tmp) const {
+        const float* x = ix.full + int64_t(v) * ix.d;
+        for (int64_t i = 0; i < ix.d; ++i) tmp[i] = double(x[i]);
+        return finish(accumulate(q, tmp, ix.d, ix.metric), ix.metric);
+    }
+};
+
+// Algorithm 1 (Sec. 2.2), "ANNS by Greedy Search": repeatedly take the first
+// unchecked node u of the candidate list C, compute distances to u's
+// unvisited neighbours (marking them visited), insert them into C, then
+// shrink C to its ef best.  Stops when C has no unchecked node or after
+// max_exp expansions (stage (2) runs a fixed number of them, Sec. 4.1 (2)).
+// C is kept sorted by (distance, id).
+template <class Neighbours, class Distance>
+void greedy_search(std::vector<Cand>& C, std::vector<uint8_t>& visited, int64_t width,
+                   Neighbours nbr, Distance dist, int ef, int64_t max_exp, Counters& cnt) {
+    for (int64_t step = 0; step < max_exp; ++step) {
+        size_t ui = C.size();
+        for (size_t i = 0; i < C.size(); ++i)
+            if (!C[i].checked) { ui = i; break; }
+        if (ui == C.size()) break;           // no unchecked node left
+        C[ui].checked = true;
+        int32_t u = C[ui].id;
+        cnt.exp += 1;
+        const int32_t* row = nbr(u);
+        for (int64_t j = 0; j < width; ++j) {
+            int32_t v = row[j];
+            if (v < 0 || visited[v]) continue;
+            visited[v] = 1;
+            float dv = dist(v);
+            cnt.dist += 1;
+            C.push_back(Cand{dv, v, false});
+        }
+        std::sort(C.begin(), C.end(), cand_less);
+        if (C.size() > size_t(ef)) C.resize(size_t(ef));
+    }
+}
+
+// Projection onto the leading dp right singular vectors, q' = q V[:, :dp]
+// (Sec. 4.1 (1): x_primary = U_{1..d'} Sigma_{1..d'} = x V_{1..d'}), in FP64.
+void project(const Index& ix, const float* q, double* qp) {
+    for (int64_t c = 0; c < ix.dp; ++c) {
+        double s = 0.0;
+        for (int64_t j = 0; j < ix.d; ++j) s += double(q[j]) * ix.basis[j * ix.dp + c];
+        qp[c] = s;
+    }
+}
+
+// The staged search of Sec. 4.1 for one query.
+void search_one(const Searcher& S, const Params& P, const float* query, int64_t qi, const Outputs& out) {
+    const Index& ix = S.ix;
+    std::vector<double> q(ix.d), qp(ix.dp), tmp(std::max(ix.d, ix.dp));
+    for (int64_t i = 0; i < ix.d; ++i) q[i] = double(query[i]);
+
+    // Stage (1) input: the projected query, stored at the paper's FP32.
+    project(ix, query, qp.data());
+    for (int64_t c = 0; c < ix.dp; ++c) qp[c] = double(float(qp[c]));
+
+    // Fast entry selection, dense form (Sec. 5 / Table 2 "FES (1 block)"):
+    // the entry vector closest to q' by (distance, id).
+    Cand entry{0.0f, ix.entry_ids[0], false};
+    if (P.use_fes) {
+        bool have = false;
+        for (int64_t e = 0; e < ix.n_entry; ++e) {
+            Cand c{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false};
+            if (!have || cand_less(c, entry)) { entry = c; have = true; }
+        }
+    } else {
+        entry.dist = S.reduced_dist(qp.data(), entry.id, tmp.data());
+    }
+
+    Counters c1, c2, c3;
+    std::vector<uint8_t> visited(ix.n, 0);
+
+    // Stage (1): Algorithm 1 over the subgraph with reduced distances.
+    std::vector<Cand> C{entry};
+    visited[entry.id] = 1;
+    if (P.stage1) {
+        greedy_search(C, visited, ix.R_sub,
+                      [&](int32_t u) { return ix.subgraph + int64_t(u) * ix.R_sub; },
+                      [&](int32_t v) { return S.reduced_dist(qp.data(), v, tmp.data()); },
+                      P.ef, INT64_MAX, c1);
+    }
+    if (out.pool1_ids) {
+        for (int j = 0; j < P.ef; ++j) {
+            bool ok = size_t(j) < C.size();
+            out.pool1_ids[qi * P.ef + j] = ok ? C[j].id : -1;
+            out.pool1_dists[qi * P.ef + j] = ok ? C[j].dist : INFINITY;
+        }
+    }
+
+    // Stage (2), part 1: full-vector distances for every candidate of stage
+    // (1), a fresh visited table holding exactly those candidates, C
+    // re-sorted and all candidates unchecked (Sec. 4.1 (2)).
+    int32_t n_rerank = 0;
+    std::fill(visited.begin(), visited.end(), 0);
+    for (Cand& c : C) {
+        c.dist = S.full_dist(q.data(), c.id, tmp.data());
+        c.checked = false;
+        visited[c.id] = 1;
+        n_rerank += 1;
+    }
+    std::sort(C.begin(), C.end(), cand_less);
+
+    // Stage (2), part 2: a fixed, small number of expansions on the subgraph
+    // with full-vector distances (the paper uses 2).
+    greedy_search(C, visited, ix.R_sub,
+                  [&](int32_t u) { return ix.subgraph + int64_t(u) * ix.R_sub; },
+                  [&](int32_t v) { return S.full_dist(q.data(), v, tmp.data()); },
+                  P.ef, P.stage2_expansions, c2);
+    if (out.pool2_ids) {
+        for (int j = 0; j < P.ef; ++j) {
+            bool ok = size_t(j) < C.size();
+            out.pool2_ids[qi * P.ef + j] = ok ? C[j].id : -1;
+            out.pool2_dists[qi * P.ef + j] = ok ? C[j].dist : INFINITY;
+        }
+    }
+
+    // Stage (3): Algorithm 1 over the full graph with full vectors, seeded by
+    // stage (2)'s candidates and reusing its visited table.  No candidate has
+    // been expanded on the full graph yet, so all start unchecked.
+    if (P.stage3) {
+        for (Cand& c : C) c.checked = false;
+        greedy_search(C, visited, ix.R,
+                      [&](int32_t u) { return ix.graph + int64_t(u) * ix.R; },
+                      [&](int32_t v) { return S.full_dist(q.data(), v, tmp.data()); },
+                      P.ef, INT64_MAX, c3);
+    }
+
+    // Output: the first k of C by (distance, id).
+    if (out.ids) {
+        for (int j = 0; j < P.k; ++j) {
+            bool ok = size_t(j) < C.size();
+            out.ids[qi * P.k + j] = ok ? C[j].id : -1;
+            out.dists[qi * P.k + j] = ok ? C[j].dist : INFINITY;
+        }
+    }
+    if (out.counters) {
+        int32_t* k = out.counters + qi * 8;
+        k[0] = c1.exp; k[1] = c1.dist; k[2] = c2.exp; k[3] = c2.dist;
+        k[4] = c3.exp; k[5] = c3.dist; k[6] = n_rerank; k[7] = entry.id;
+    }
+}
+
+template <class F>
+void parallel_for(int64_t n, int nthreads, F f) {
+    if (nthreads <= 1 || n <= 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back([&, t] {
+            for (int64_t i = t; i < n; i += nthreads) f(i);
+        });
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+// Staged search of Sec. 4.1 over nq queries (nq x d FP32, row-major).
+// Returns 0 on success, -1 on invalid arguments.
+int oracle_search(const Index* ix, const Params* P, const float* queries, int64_t nq, const Outputs* out) {
+    if (!ix || !P || P->k < 1 || P->ef < P->k || ix->n_entry < 1) return -1;
+    Searcher S(*ix);
+    parallel_for(nq, P->nthreads, [&](int64_t qi) { search_one(S, *P, queries + qi * ix->d, qi, *out); });
+    return 0;
+}
+
+// q' = round_FP32(q V[:, :dp]) per component, plus the unrounded FP64 value.
+int oracle_project(const Index* ix, const float* queries, int64_t nq, double* out_f64, float* out_f32) {
+    std::vector<double> qp(ix->dp);
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        project(*ix, queries + qi * ix->d, qp.data());
+        for (int64_t c = 0; c < ix->dp; ++c) {
+            if (out_f64) out_f64[qi * ix->dp + c] = qp[c];
+            if (out_f32) out_f32[qi * ix->dp + c] = float(qp[c]);
+        }
+    }
+    return 0;
+}
+
+// Dense FES alone: for each projected query (nq x dp FP32), the entry with
+// the smallest (FP32 distance, id) and that distance.
+int oracle_fes(const Index* ix, const float* qproj, int64_t nq, int32_t* out_entry, float* out_dist) {
+    Searcher S(*ix);
+    std::vector<double> qp(ix->dp), tmp(ix->dp);
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        for (int64_t c = 0; c < ix->dp; ++c) qp[c] = double(qproj[qi * ix->dp + c]);
+        Cand best{INFINITY, -1, false};
+        for (int64_t e = 0; e < ix->n_entry; ++e) {
+            Cand c{S.reduced_dist(qp.data(), ix->entry_ids[e], tmp.data()), ix->entry_ids[e], false};
+            if (best.id < 0 || cand_less(c, best)) best = c;
+        }
+        out_entry[qi] = best.id;
+        out_dist[qi] = best.dist;
+    }
+    return 0;
+}
+
+// Exact FP64 brute-force top-k over the full vectors (recall ground truth,
+// Sec. 6.1 "Metrics"): smallest (FP64 distance, id), distances in FP64.
+int oracle_bruteforce(const float* base, int64_t n, int64_t d, int metric, const float* queries, int64_t nq,
+                      int k, int nthreads, int32_t* out_ids, double* out_dists) {
+    parallel_for(nq, nthreads, [&](int64_t qi) {
+        std::vector<std::pair<double, int32_t>> all(n);
+        const float* q = queries + qi * d;
+        for (int64_t v = 0; v < n; ++v) {
+            const float* x = base + v * d;
+            double s = 0.0;
+            for (int64_t i = 0; i < d; ++i) {
+                if (metric == 0) {
+                    double t = double(q[i]) - double(x[i]);
+                    s += t * t;
+                } else {
+                    s += double(q[i]) * double(x[i]);
+                }
+            }
+            all[v] = {metric == 0 ? s : -s, int32_t(v)};
+        }
+        int kk = int(std::min<int64_t>(k, n));
+        std::partial_sort(all.begin(), all.begin() + kk, all.end());
+        for (int j = 0; j < k; ++j) {
+            out_ids[qi * k + j] = j < kk ? all[j].second : -1;
+            out_dists[qi * k + j] = j < kk ? all[j].first : INFINITY;
+        }
+    });
+    return 0;
+}
+
+// Exposed decoders so the tests can pin them against the format tables.
+double oracle_decode_e4m3(uint8_t c) { return decode_e4m3(c); }
+double oracle_decode_bf16(uint16_t h) { return decode_bf16(h); }
+
+int oracle_abi_version(void) { return 1; }
+
+}  // extern "C"

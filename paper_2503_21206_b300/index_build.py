@@ -1,0 +1,462 @@
+"""Offline index preparation (Sec. 3 / Fig. 2 steps (a)-(c); Sec. 4.1 (1)).
+
+Builds, from a base set X, every input the search reads:
+
+* the full graph (a): exact 2R-nearest candidates, the HNSW neighbour-selection
+  heuristic to R, reverse edges, re-selection, and a reachability repair from
+  the entry set so that every node can be reached;
+* the subgraph (b): a seeded uniform node sample, re-connected by the same
+  construction among the sampled nodes, stored in the full id space with
+  zero-degree rows for unsampled nodes (Sec. 4.3);
+* the compact vectors (c): the right singular vectors V of an FP64 SVD of a
+  row sample, and the reduced rows x V[:, :d'] of the sampled nodes in FP32,
+  BF16 or FP8 E4M3 with per-row FP32 scales;
+* a seeded uniform entry set of sampled nodes for fast entry selection.
+
+It also writes / reads the on-disk index format and computes certified exact
+ground truth for recall.  This is input generation: it is not timed and holds
+none of the search arithmetic.  torch is used for its matrix products (on the
+GPU when one is given) and numpy for the FP64 SVD.
+"""
+from __future__ import annotations
+
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .synth import Workload
+
+DTYPE_CODES = {"f32": 0, "bf16": 1, "fp8": 2}
+FILE_MAGIC = "pilot-index 1"
+
+
+@dataclass
+class PilotIndexData:
+    """Host arrays of one index (layout of the C-ABI ``pilot_index_desc``)."""
+    graph: np.ndarray            # n x R int32, original ids, -1 padded
+    subgraph_mask: np.ndarray    # n uint8
+    subgraph: np.ndarray         # n x R_sub int32, original ids, -1 padded
+    basis: np.ndarray            # d x dp float64
+    reduced: np.ndarray          # n_sub x dp: float32 | uint16 (bf16 bits) | uint8 (e4m3 codes)
+    reduced_dtype: str           # "f32" | "bf16" | "fp8"
+    reduced_scales: np.ndarray | None   # n_sub float32 (fp8)
+    full: np.ndarray             # n x d float32
+    entry_ids: np.ndarray        # n_entry int32
+    metric: int                  # 0 L2, 1 IP
+
+    @property
+    def n(self):
+        return self.full.shape[0]
+
+    @property
+    def d(self):
+        return self.full.shape[1]
+
+    @property
+    def dp(self):
+        return self.basis.shape[1]
+
+    def with_reduced(self, dtype: str, reduced_f32: np.ndarray) -> "PilotIndexData":
+        """A copy whose reduced rows are ``reduced_f32`` stored as ``dtype``."""
+        red, sc = quantize_rows(reduced_f32, dtype)
+        return PilotIndexData(self.graph, self.subgraph_mask, self.subgraph, self.basis, red, dtype, sc,
+                              self.full, self.entry_ids, self.metric)
+
+
+# ------------------------------------------------------------------ kNN --
+
+def _dev(device):
+    return torch.device(device if device is not None else "cpu")
+
+
+def knn_candidates(X: np.ndarray, k: int, device=None, chunk: int = 4096, exclude_self: bool = True):
+    """Exact k nearest neighbours of every row of X among the rows of X by
+    squared L2 (FP32), ordered by (distance, id).  Returns (ids, dists)."""
+    dev = _dev(device)
+    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    n = Xt.shape[0]
+    norms = (Xt.double() ** 2).sum(1).float()
+    k_eff = min(k, n - 1 if exclude_self else n)
+    ids = torch.empty((n, k_eff), dtype=torch.int64, device=dev)
+    dst = torch.empty((n, k_eff), dtype=torch.float32, device=dev)
+    extra = 8
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        D = norms[s:e, None] - 2.0 * (Xt[s:e] @ Xt.T) + norms[None, :]
+        if exclude_self:
+            D[torch.arange(e - s, device=dev), torch.arange(s, e, device=dev)] = float("inf")
+        kk = min(k_eff + extra, n)
+        vals, idx = torch.topk(D, kk, dim=1, largest=False)
+        # exact FP32 distances of the candidates, then order by (dist, id)
+        diff = Xt[s:e, None, :] - Xt[idx]
+        ex = (diff * diff).sum(-1)
+        if exclude_self:
+            ex = torch.where(idx == torch.arange(s, e, device=dev)[:, None], torch.full_like(ex, float("inf")), ex)
+        o1 = torch.argsort(idx, dim=1, stable=True)
+        ex, idx = torch.gather(ex, 1, o1), torch.gather(idx, 1, o1)
+        o2 = torch.argsort(ex, dim=1, stable=True)
+        ex, idx = torch.gather(ex, 1, o2), torch.gather(idx, 1, o2)
+        ids[s:e] = idx[:, :k_eff]
+        dst[s:e] = ex[:, :k_eff]
+    return ids, dst
+
+
+def _pair_dists(Xt, cand):
+    """Squared L2 between every pair of candidates of each row: B x C x C."""
+    valid = cand >= 0
+    V = Xt[cand.clamp(min=0)]
+    n2 = (V * V).sum(-1)
+    P = n2[:, :, None] + n2[:, None, :] - 2.0 * torch.bmm(V, V.transpose(1, 2))
+    P = P.clamp(min=0)
+    P[~(valid[:, :, None] & valid[:, None, :])] = float("inf")
+    return P
+
+
+def select_neighbours(Xt: torch.Tensor, node: torch.Tensor, cand: torch.Tensor, dq: torch.Tensor, R: int):
+    """HNSW neighbour-selection heuristic, vectorised over rows: walk the
+    candidates of each node in (distance, id) order and keep c unless some
+    already kept r is closer to c than the node is (dist(c, r) <= dist(c, node)),
+    up to R kept.  cand: B x C (-1 = none), dq: B x C distances to the node."""
+    B, C = cand.shape
+    P = _pair_dists(Xt, cand)
+    keep = torch.zeros((B, C), dtype=torch.bool, device=cand.device)
+    nk = torch.zeros(B, dtype=torch.int64, device=cand.device)
+    for j in range(C):
+        ok = (cand[:, j] >= 0) & (cand[:, j] != node) & (nk < R)
+        if j > 0:
+            viol = (keep[:, :j] & (P[:, j, :j] <= dq[:, j:j + 1])).any(1)
+            ok &= ~viol
+        keep[:, j] = ok
+        nk += ok.long()
+    # first R kept, in candidate order
+    order = torch.argsort((~keep).to(torch.int8), dim=1, stable=True)[:, :R]
+    out = torch.gather(cand, 1, order)
+    kept = torch.gather(keep, 1, order)
+    return torch.where(kept, out, torch.full_like(out, -1))
+
+
+def build_graph(X: np.ndarray, R: int, entries_local: np.ndarray, device=None, chunk: int = 16384,
+                verbose: bool = False) -> np.ndarray:
+    """Out-degree-R graph over the rows of X (local ids), -1 padded."""
+    dev = _dev(device)
+    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    n = Xt.shape[0]
+    C = min(2 * R, n - 1)
+    cand, cd = knn_candidates(X, C, device=device)
+    adj = torch.full((n, R), -1, dtype=torch.int64, device=dev)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        adj[s:e] = select_neighbours(Xt, torch.arange(s, e, device=dev), cand[s:e], cd[s:e], R)
+    # reverse edges: each node also considers the (up to 2R) closest nodes that
+    # selected it, then the union is re-selected to R.
+    src = torch.arange(n, device=dev)[:, None].expand(n, R)
+    m = adj >= 0
+    es, ed = src[m], adj[m]
+    edist = ((Xt[es] - Xt[ed]) ** 2).sum(-1)
+    o = torch.argsort(edist, stable=True)
+    es, ed, edist = es[o], ed[o], edist[o]
+    o = torch.argsort(ed, stable=True)
+    es, ed, edist = es[o], ed[o], edist[o]
+    counts = torch.bincount(ed, minlength=n)
+    starts = torch.cumsum(counts, 0) - counts
+    rank = torch.arange(ed.numel(), device=dev) - starts[ed]
+    Rrev = 2 * R
+    sel = rank < Rrev
+    rev = torch.full((n, Rrev), -1, dtype=torch.int64, device=dev)
+    rev[ed[sel], rank[sel]] = es[sel]
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        cand2 = torch.cat([adj[s:e], rev[s:e]], 1)
+        cs, _ = torch.sort(cand2, dim=1)
+        dup = torch.zeros_like(cs, dtype=torch.bool)
+        dup[:, 1:] = cs[:, 1:] == cs[:, :-1]
+        cs = torch.where(dup, torch.full_like(cs, -1), cs)
+        valid = cs >= 0
+        diff = Xt[s:e, None, :] - Xt[cs.clamp(min=0)]
+        dq = (diff * diff).sum(-1)
+        dq = torch.where(valid, dq, torch.full_like(dq, float("inf")))
+        o1 = torch.argsort(torch.where(valid, cs, torch.full_like(cs, n)), dim=1, stable=True)
+        cs, dq = torch.gather(cs, 1, o1), torch.gather(dq, 1, o1)
+        o2 = torch.argsort(dq, dim=1, stable=True)
+        cs, dq = torch.gather(cs, 1, o2), torch.gather(dq, 1, o2)
+        adj[s:e] = select_neighbours(Xt, torch.arange(s, e, device=dev), cs, dq, R)
+    adj_np = adj.cpu().numpy().astype(np.int32)
+    repair_reachability(X, adj_np, entries_local, device=device, verbose=verbose)
+    return adj_np
+
+
+def _reached_from(adj: np.ndarray, sources: np.ndarray) -> np.ndarray:
+    """Boolean mask of the nodes reachable from ``sources`` along the edges."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    n, R = adj.shape
+    rows = np.repeat(np.arange(n + 1), np.r_[np.full(n, R), [len(sources)]])
+    cols = np.concatenate([adj.reshape(-1), sources.astype(np.int32)])
+    keep = cols >= 0
+    g = sp.csr_matrix((np.ones(int(keep.sum()), np.int8), (rows[keep], cols[keep])), shape=(n + 1, n + 1))
+    order = breadth_first_order(g, n, directed=True, return_predecessors=False)
+    mask = np.zeros(n + 1, bool)
+    mask[order] = True
+    return mask[:n]
+
+
+def repair_reachability(X: np.ndarray, adj: np.ndarray, sources: np.ndarray, device=None,
+                        verbose: bool = False, max_rounds: int = 10_000) -> int:
+    """Make every node reachable from ``sources`` (in place).
+
+    Each round links every unreached node that no other unreached node points
+    to (or, if none, the unreached node closest to the reached set) from its
+    nearest reached node with a free adjacency slot.  Returns edges added."""
+    dev = _dev(device)
+    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    n, R = adj.shape
+    added = 0
+    for _ in range(max_rounds):
+        reached = _reached_from(adj, sources)
+        U = np.nonzero(~reached)[0]
+        if U.size == 0:
+            return added
+        inU = np.zeros(n, bool)
+        inU[U] = True
+        tgt = adj[U].reshape(-1)
+        tgt = tgt[tgt >= 0]
+        pointed = np.zeros(n, bool)
+        pointed[tgt[inU[tgt]]] = True
+        S = U[~pointed[U]]
+        free = (adj < 0).any(1) & reached
+        F = np.nonzero(free)[0]
+        if F.size == 0:
+            F = np.nonzero(reached)[0]
+        pick = S if S.size else U
+        Xs = Xt[torch.from_numpy(pick).to(dev)]
+        Xf = Xt[torch.from_numpy(F).to(dev)]
+        kk = min(8, F.size)
+        best_d = []
+        best_i = []
+        for s in range(0, Xs.shape[0], 2048):
+            D = (Xs[s:s + 2048] ** 2).sum(1)[:, None] - 2 * Xs[s:s + 2048] @ Xf.T + (Xf ** 2).sum(1)[None, :]
+            v, i = torch.topk(D, kk, dim=1, largest=False)
+            best_d.append(v.cpu())
+            best_i.append(i.cpu())
+        bd = torch.cat(best_d).numpy()
+        bi = F[torch.cat(best_i).numpy()]
+        if not S.size:   # only cycles remain: link the single closest node
+            j = int(np.argmin(bd[:, 0]))
+            pick, bd, bi = pick[j:j + 1], bd[j:j + 1], bi[j:j + 1]
+        for u, cands in zip(pick, bi):
+            placed = False
+            for r in cands:
+                slots = np.nonzero(adj[r] < 0)[0]
+                if slots.size:
+                    adj[r, slots[0]] = u
+                    placed = True
+                    break
+            if not placed:          # every candidate is full: overwrite the last slot
+                adj[cands[0], R - 1] = u
+            added += 1
+        if verbose:
+            print(f"repair: {U.size} unreached, linked {len(pick)}")
+    raise RuntimeError("reachability repair did not converge")
+
+
+# -------------------------------------------------------------- SVD (c) --
+
+def svd_basis(X: np.ndarray, seed: int, max_rows: int = 262_144) -> np.ndarray:
+    """Right singular vectors V (d x d, FP64) of a seeded row sample of X,
+    uncentred (Sec. 4.1 (1): X = U Sigma V^T), columns by decreasing singular
+    value, each column's largest-magnitude component made positive."""
+    rng = np.random.default_rng(seed)
+    n = X.shape[0]
+    rows = np.sort(rng.choice(n, size=min(n, max_rows), replace=False))
+    A = X[rows].astype(np.float64)
+    _, _, vt = np.linalg.svd(A, full_matrices=False)
+    V = vt.T.copy()
+    if V.shape[1] < X.shape[1]:   # fewer rows than columns: complete the basis
+        q, _ = np.linalg.qr(np.concatenate([V, np.eye(X.shape[1])], 1))
+        V = q[:, :X.shape[1]]
+    piv = np.argmax(np.abs(V), axis=0)
+    V *= np.sign(V[piv, np.arange(V.shape[1])])[None, :]
+    return V
+
+
+def project_rows(X: np.ndarray, basis: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
+    """x V[:, :dp] in FP64, rounded to FP32."""
+    out = np.empty((X.shape[0], basis.shape[1]), np.float32)
+    for s in range(0, X.shape[0], chunk):
+        out[s:s + chunk] = (X[s:s + chunk].astype(np.float64) @ basis).astype(np.float32)
+    return out
+
+
+def quantize_rows(red: np.ndarray, dtype: str):
+    """Store FP32 reduced rows as FP32, BF16 (round to nearest even) or FP8
+    E4M3 with scale_r = max|x_r| / 448 (1 for an all-zero row) and codes
+    RNE(x / scale) saturated to +-448."""
+    if dtype == "f32":
+        return np.ascontiguousarray(red, np.float32), None
+    t = torch.from_numpy(np.ascontiguousarray(red, np.float32))
+    if dtype == "bf16":
+        return t.to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16).copy(), None
+    if dtype == "fp8":
+        amax = t.abs().amax(1)
+        scale = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax))
+        codes = (t / scale[:, None]).clamp(-448.0, 448.0).to(torch.float8_e4m3fn)
+        return codes.view(torch.uint8).numpy().copy(), scale.numpy().astype(np.float32)
+    raise ValueError(dtype)
+
+
+# ------------------------------------------------------------ the index --
+
+def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int, n_entry: int, metric: int,
+                seed_graph: int, seed_entry: int, reduced_dtype: str = "f32", device=None,
+                verbose: bool = False, keep_reduced_f32: bool = False):
+    """Every search input for base set X (see module docstring)."""
+    n, d = X.shape
+    rng = np.random.default_rng(seed_graph)
+    n_sub = max(1, int(round(sample_ratio * n)))
+    sampled = np.sort(rng.choice(n, size=n_sub, replace=False)).astype(np.int64)
+    erng = np.random.default_rng(seed_entry)
+    n_entry = min(n_entry, n_sub)
+    entry_local = np.sort(erng.choice(n_sub, size=n_entry, replace=False))
+    entry_ids = sampled[entry_local].astype(np.int32)
+
+    graph = build_graph(X, R, entry_ids, device=device, verbose=verbose)
+    sub_local = build_graph(X[sampled], R_sub, entry_local, device=device, verbose=verbose)
+    subgraph = np.full((n, R_sub), -1, np.int32)
+    subgraph[sampled] = np.where(sub_local >= 0, sampled[np.maximum(sub_local, 0)], -1).astype(np.int32)
+    mask = np.zeros(n, np.uint8)
+    mask[sampled] = 1
+
+    V = svd_basis(X, seed_graph)
+    basis = np.ascontiguousarray(V[:, :dp])
+    red32 = project_rows(X[sampled], basis)
+    red, scales = quantize_rows(red32, reduced_dtype)
+    idx = PilotIndexData(graph, mask, subgraph, basis, red, reduced_dtype, scales,
+                         np.ascontiguousarray(X, np.float32), entry_ids, metric)
+    if keep_reduced_f32:
+        return idx, red32, V
+    return idx
+
+
+def build_workload(w: Workload, device=None, n: int | None = None, nq: int | None = None,
+                   reduced_dtype: str | None = None, verbose: bool = False):
+    """(index, queries, reduced FP32 rows, full basis V) for a workload."""
+    from .synth import generate
+    X, Q = generate(w, n=n, nq=nq)
+    rd = reduced_dtype or w.reduced_dtypes[0]
+    idx, red32, V = build_index(X, w.R, w.R_sub, w.sample_ratio, w.dp, w.n_entry, w.metric, w.graph_seed,
+                                w.entry_seed, rd, device=device, verbose=verbose, keep_reduced_f32=True)
+    return idx, Q, red32, V
+
+
+# ------------------------------------------------------------ files --
+
+_FILES = [("graph", "i32"), ("subgraph_mask", "u8"), ("subgraph", "i32"), ("basis", "f64"),
+          ("reduced", None), ("reduced_scales", "f32"), ("full", "f32"), ("entry_ids", "i32")]
+_NP = {"i32": np.int32, "u8": np.uint8, "f64": np.float64, "f32": np.float32, "u16": np.uint16}
+
+
+def checksum64(a: np.ndarray) -> int:
+    """Position-weighted word sum: the bytes zero-padded to 8-byte words w_i,
+    sum_i w_i * (2i + 1) modulo 2^64.  The C loader computes the same."""
+    b = a.tobytes()
+    b += b"\0" * (-len(b) % 8)
+    w = np.frombuffer(b, dtype="<u8")
+    with np.errstate(over="ignore"):
+        return int((w * (2 * np.arange(w.size, dtype=np.uint64) + np.uint64(1))).sum(dtype=np.uint64))
+
+
+def save_index(idx: PilotIndexData, path: str) -> None:
+    """Write the directory format read by ``pilot_index_load_files``:
+    ``pilot_index.txt`` ("key value" lines) plus one raw little-endian file
+    per array.  Each array line carries its byte count."""
+    os.makedirs(path, exist_ok=True)
+    n, d = idx.full.shape
+    lines = [FILE_MAGIC, f"n {n}", f"d {d}", f"dp {idx.dp}", f"R {idx.graph.shape[1]}",
+             f"R_sub {idx.subgraph.shape[1]}", f"n_sub {int(idx.subgraph_mask.sum())}",
+             f"n_entry {idx.entry_ids.shape[0]}", f"metric {idx.metric}",
+             f"reduced_dtype {DTYPE_CODES[idx.reduced_dtype]}"]
+    for name, kind in _FILES:
+        a = getattr(idx, name)
+        if a is None:
+            continue
+        kind = kind or {"f32": "f32", "bf16": "u16", "fp8": "u8"}[idx.reduced_dtype]
+        a = np.ascontiguousarray(a, _NP[kind])
+        with open(os.path.join(path, name + ".bin"), "wb") as f:
+            f.write(a.tobytes())
+        lines.append(f"array {name} {kind} {a.nbytes} {checksum64(a):016x}")
+    with open(os.path.join(path, "pilot_index.txt"), "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def load_index(path: str) -> PilotIndexData:
+    meta, arrays = {}, {}
+    with open(os.path.join(path, "pilot_index.txt")) as f:
+        lines = f.read().split("\n")
+    assert lines[0] == FILE_MAGIC
+    for ln in lines[1:]:
+        if not ln:
+            continue
+        p = ln.split()
+        if p[0] == "array":
+            arrays[p[1]] = np.fromfile(os.path.join(path, p[1] + ".bin"), dtype=_NP[p[2]])
+        else:
+            meta[p[0]] = int(p[1])
+    n, d, dp = meta["n"], meta["d"], meta["dp"]
+    rdt = {v: k for k, v in DTYPE_CODES.items()}[meta["reduced_dtype"]]
+    return PilotIndexData(arrays["graph"].reshape(n, meta["R"]), arrays["subgraph_mask"],
+                          arrays["subgraph"].reshape(n, meta["R_sub"]), arrays["basis"].reshape(d, dp),
+                          arrays["reduced"].reshape(meta["n_sub"], dp), rdt, arrays.get("reduced_scales"),
+                          arrays["full"].reshape(n, d), arrays["entry_ids"], meta["metric"])
+
+
+# ------------------------------------------------------ ground truth --
+
+def exact_topk(X: np.ndarray, Q: np.ndarray, k: int, metric: int = 0, device=None, margin: int = 32,
+               chunk: int = 1024):
+    """Exact FP64 top-k ids by (FP64 distance, id) for every query.
+
+    Candidates come from an FP32 matrix product (top k+margin); their distances
+    are recomputed in FP64.  A query is certified when the (k+margin)-th FP32
+    score, less a bound on the FP32 error, exceeds the k-th FP64 distance;
+    uncertified queries are recomputed over all rows in FP64."""
+    dev = _dev(device)
+    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    xn = (Xt.double() ** 2).sum(1)
+    n, d = X.shape
+    kk = min(k + margin, n)
+    ids_out = np.empty((Q.shape[0], k), np.int32)
+    d_out = np.empty((Q.shape[0], k), np.float64)
+    X64 = X.astype(np.float64) if n * d <= 50_000_000 else None
+    for s in range(0, Q.shape[0], chunk):
+        Qt = torch.from_numpy(np.ascontiguousarray(Q[s:s + chunk], np.float32)).to(dev)
+        ip = Qt @ Xt.T
+        if metric == 0:
+            qn = (Qt.double() ** 2).sum(1)
+            score = (qn[:, None].float() + xn[None, :].float() - 2 * ip)
+        else:
+            score = -ip
+        vals, idx = torch.topk(score, kk, dim=1, largest=False)
+        vals, idx = vals.cpu().numpy().astype(np.float64), idx.cpu().numpy()
+        q64 = Q[s:s + chunk].astype(np.float64)
+        xc = X[idx].astype(np.float64)
+        if metric == 0:
+            ex = ((q64[:, None, :] - xc) ** 2).sum(-1)
+        else:
+            ex = -(q64[:, None, :] * xc).sum(-1)
+        qnorm = np.linalg.norm(q64, axis=1)
+        xmax = float(np.sqrt(xn.max().item()))
+        bound = 4.0 * (d + 2) * 2.0 ** -23 * (qnorm + xmax) ** 2 + 1e-30
+        for i in range(ex.shape[0]):
+            order = np.lexsort((idx[i], ex[i]))
+            top_ids, top_d = idx[i][order][:k], ex[i][order][:k]
+            if kk < n and not (vals[i, -1] - bound[i] > top_d[-1]):
+                # not certified: exact FP64 over every row
+                xr = X64 if X64 is not None else X.astype(np.float64)
+                full = ((q64[i] - xr) ** 2).sum(1) if metric == 0 else -(xr @ q64[i])
+                o = np.lexsort((np.arange(n), full))[:k]
+                top_ids, top_d = o, full[o]
+            ids_out[s + i] = top_ids
+            d_out[s + i] = top_d
+    return ids_out, d_out
