@@ -1,0 +1,162 @@
+/*
+ * pilot.h -- C ABI of libpilot, a B300 (sm_103a) implementation of the GPU
+ * search stages of PilotANN (Gui et al., arxiv 2503.21206).
+ *
+ * A search runs, for every query, the staged method of Sec. 4.1:
+ *   project   q' = q V[:, :d']                        (Sec. 4.1 (1), SVD)
+ *   FES       entry = argmin_e dist(q', e')           (Sec. 5, dense form of Table 2)
+ *   stage (1) Algorithm 1 on the sampled subgraph with reduced vectors
+ *   stage (2) full-vector re-rank of stage (1)'s candidates, then a fixed
+ *             number (default 2) of subgraph expansions with full vectors
+ *   stage (3) Algorithm 1 on the full graph with full vectors, seeded by
+ *             stage (2)'s candidates and visited table (Sec. 4.1 (3))
+ * and returns the first k candidates by (distance, id).
+ *
+ * Numerics: each distance (squared L2, or -<q,x> for inner product) and each
+ * projected query component is the FP32 rounding of its exact value, the
+ * paper's FP32 precision (Sec. 6.1); ties are broken by the smaller node id.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a pilot_status; nothing aborts or prints.  On error
+ *    pilot_last_error() returns a message for the calling thread.
+ *  - Node ids are int32 original (full-graph) ids, 0 <= id < n < 2^31.
+ *  - All arrays are dense, row-major, little-endian.
+ */
+#ifndef PILOT_H
+#define PILOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pilot_index pilot_index;    /* opaque, owned by the library */
+typedef struct pilot_server pilot_server;  /* opaque, owned by the library */
+
+typedef enum {
+    PILOT_OK = 0,
+    PILOT_EINVAL = 1,    /* an argument is out of range or malformed */
+    PILOT_ENOMEM = 2,    /* a device or pinned host allocation failed */
+    PILOT_ECUDA = 3,     /* a CUDA runtime call failed */
+    PILOT_EIO = 4,       /* a file could not be opened or read */
+    PILOT_ETIMEOUT = 5,  /* a bounded wait ran out */
+    PILOT_EBUSY = 6,     /* no capacity now (serving admission) */
+    PILOT_EFORMAT = 7    /* an index file has a bad header, size or checksum */
+} pilot_status;
+
+enum { PILOT_METRIC_L2 = 0, PILOT_METRIC_IP = 1 };
+enum { PILOT_REDUCED_F32 = 0, PILOT_REDUCED_BF16 = 1, PILOT_REDUCED_FP8_E4M3 = 2 };
+
+/* Largest candidate-list size ef a search accepts. */
+#define PILOT_MAX_EF 512
+/* Largest graph / subgraph out-degree. */
+#define PILOT_MAX_DEGREE 64
+
+/*
+ * Index description (Sec. 3, Fig. 2 (a)-(c); Sec. 4.3).  All pointers are
+ * HOST pointers; pilot_index_load copies everything into library-owned device
+ * memory, so the caller may free them as soon as the call returns.
+ *
+ *  graph           n x R int32, full graph, -1 padded
+ *  subgraph_mask   n uint8, 1 = node kept by subgraph sampling
+ *  subgraph        n x R_sub int32 in the full id space (Sec. 4.3): rows of
+ *                  unsampled nodes hold only -1; every listed id is sampled
+ *  svd_basis       d x dp float64, column c = right singular vector c
+ *                  (Sec. 4.1 (1), X = U S V^T); the leading dp columns
+ *  reduced_vecs    n_sub x dp reduced rows x V[:, :dp] of the sampled nodes in
+ *                  ascending original-id order; float32, bf16 bits (uint16) or
+ *                  FP8 E4M3 "fn" codes (uint8) as given by reduced_dtype
+ *  reduced_scales  n_sub float32 per-row scales (FP8 only, else NULL):
+ *                  value = decode(code) * scale
+ *  full_vecs       n x d float32 original vectors
+ *  entry_ids       n_entry int32 FES entry set, each a sampled node
+ *
+ * Rejected with PILOT_EINVAL: sizes out of range (n >= 2^31, R or R_sub above
+ * PILOT_MAX_DEGREE, dp > d, n_entry < 1), an id outside [-1, n), a repeated id
+ * within a row, a subgraph edge to an unsampled node, an entry that is not
+ * sampled, a non-finite vector or basis value.
+ */
+typedef struct {
+    int64_t n, d, dp, R, R_sub, n_entry;
+    int32_t metric;                 /* PILOT_METRIC_* */
+    int32_t reduced_dtype;          /* PILOT_REDUCED_* */
+    const int32_t* graph;
+    const uint8_t* subgraph_mask;
+    const int32_t* subgraph;
+    const double* svd_basis;
+    const void* reduced_vecs;
+    const float* reduced_scales;
+    const float* full_vecs;
+    const int32_t* entry_ids;
+} pilot_index_desc;
+
+/* Copy an index to the current CUDA device.  *out receives the handle. */
+pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
+
+/*
+ * Load an index directory written by the offline builder: "pilot_index.txt"
+ * (first line "pilot-index 1", then "key value" lines and one
+ * "array <name> <i32|u8|u16|f32|f64> <bytes> <checksum hex>" line per array)
+ * plus "<name>.bin" raw files.  The checksum is sum_i w_i * (2i + 1) mod 2^64
+ * over the file's bytes as zero-padded little-endian 64-bit words w_i.
+ * flags must be 0.  PILOT_EIO if a file is missing, PILOT_EFORMAT on a bad
+ * header, size or checksum; then the same validation as pilot_index_load.
+ */
+pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** out);
+
+/* Release an index and its device memory.  NULL is ignored. */
+void pilot_index_free(pilot_index* index);
+
+/* Sizes of a loaded index (any pointer may be NULL). */
+pilot_status pilot_index_info(const pilot_index* index, int64_t* n, int64_t* d, int64_t* dp, int64_t* n_sub,
+                              int64_t* device_bytes);
+
+/*
+ * Search options.  Zero-initialise, then set what differs from the paper's
+ * defaults: pilot_search_options_default() fills them in.
+ */
+typedef struct {
+    int32_t stage1;             /* 1: run stage (1) (default 1) */
+    int32_t stage2_expansions;  /* stage (2) subgraph expansions (default 2, Sec. 4.1 (2)) */
+    int32_t stage3;             /* 1: run stage (3) (default 1) */
+    int32_t use_fes;            /* 1: FES entry (default); 0: entry_ids[0] */
+    int32_t hash_log2;          /* visited table 2^hash_log2 slots per query; 0 = automatic */
+    int32_t warps_per_block;    /* 0 = automatic */
+    int32_t* counters;          /* optional nq x 8 int32 (host or device): per query the
+                                   expansions and distances of stages (1), (2), (3), the
+                                   number of re-ranked candidates and the entry id */
+} pilot_search_options;
+
+void pilot_search_options_default(pilot_search_options* opt);
+
+/*
+ * Top-k search of nq queries (Sec. 4.1).
+ *  queries    nq x d float32, host or device pointer
+ *  out_ids    nq x k int32 original ids, -1 where fewer than k were found
+ *  out_dists  nq x k float32 distances, +inf where fewer than k were found
+ *  stream     a cudaStream_t, or NULL for the default stream
+ * Host and device pointers may be mixed; the library tells them apart.  The
+ * call is synchronous: when it returns the results are written.
+ * PILOT_EINVAL if k < 1, ef < k, ef > PILOT_MAX_EF, nq < 0, or a query holds a
+ * NaN or infinity (the other queries' results are still written).
+ */
+pilot_status pilot_search(pilot_index* index, const float* queries, int64_t nq, int k, int ef, int32_t* out_ids,
+                          float* out_dists, void* stream);
+
+/* pilot_search with explicit options (NULL = defaults). */
+pilot_status pilot_search_ex(pilot_index* index, const float* queries, int64_t nq, int k, int ef,
+                             int32_t* out_ids, float* out_dists, void* stream, const pilot_search_options* opt);
+
+/* The calling thread's last error message ("" if none). */
+const char* pilot_last_error(void);
+
+/* Library and ABI version, e.g. 1. */
+int pilot_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PILOT_H */

@@ -1,0 +1,213 @@
+// device_common.cuh -- device helpers shared by the search kernels.
+//
+// Numerics.  The paper computes every distance in FP32 (Sec. 6.1).  Here each
+// distance is the FP32 rounding of its exact value: the sum is carried as an
+// unevaluated pair hi + lo of FP32 numbers built from error-free
+// transformations -- Knuth's TwoSum and the FMA-based TwoProduct (as used in
+// Ogita, Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 2005) -- and rounded once at the end.  The result is independent of the
+// order in which lanes combine partial sums except in the rare case where the
+// exact value lies within ~2^-40 (relative) of an FP32 rounding boundary.
+#pragma once
+
+#include <cstdint>
+
+namespace pilot {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint64_t kKeyEmpty = ~0ull;
+constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------ FP32 pairs --
+
+struct DF {
+    float hi, lo;
+};
+
+// s + e == a + b exactly (Knuth).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    float s = __fadd_rn(a, b);
+    float bv = __fsub_rn(s, a);
+    float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+    return s;
+}
+
+// p + e == a * b exactly (FMA).
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+    float p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// acc += (q - x)^2 with q - x = d + e exact, (d + e)^2 ~= d*d + 2de; d*d is
+// split exactly, the small terms go to acc.lo.
+__device__ __forceinline__ void l2_acc(DF& acc, float q, float x) {
+    float e;
+    float d = two_sum(q, -x, e);
+    float pe;
+    float p = two_prod(d, d, pe);
+    float t;
+    acc.hi = two_sum(acc.hi, p, t);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, __fmaf_rn(__fmul_rn(2.0f, d), e, pe)));
+}
+
+// Same with x = xh + xl given exactly as two FP32 numbers (FP8 code * scale).
+__device__ __forceinline__ void l2_acc2(DF& acc, float q, float xh, float xl) {
+    float e;
+    float d = two_sum(q, -xh, e);
+    e = __fsub_rn(e, xl);
+    float pe;
+    float p = two_prod(d, d, pe);
+    float t;
+    acc.hi = two_sum(acc.hi, p, t);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, __fmaf_rn(__fmul_rn(2.0f, d), e, pe)));
+}
+
+// acc += q * x.
+__device__ __forceinline__ void ip_acc(DF& acc, float q, float x) {
+    float pe;
+    float p = two_prod(q, x, pe);
+    float t;
+    acc.hi = two_sum(acc.hi, p, t);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, pe));
+}
+
+__device__ __forceinline__ void ip_acc2(DF& acc, float q, float xh, float xl) {
+    float pe;
+    float p = two_prod(q, xh, pe);
+    pe = __fmaf_rn(q, xl, pe);
+    float t;
+    acc.hi = two_sum(acc.hi, p, t);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, pe));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float e;
+    float s = two_sum(a.hi, b.hi, e);
+    float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    float hi = __fadd_rn(s, lo);
+    DF r;
+    r.lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    r.hi = hi;
+    return r;
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF v, int m) {
+    DF r;
+    r.hi = __shfl_xor_sync(kFull, v.hi, m);
+    r.lo = __shfl_xor_sync(kFull, v.lo, m);
+    return r;
+}
+
+// One rounding of hi + lo; the inner-product metric reports -<q, x>.
+__device__ __forceinline__ float df_finish(DF a, int metric) {
+    float r = __fadd_rn(a.hi, a.lo);
+    if (metric == 1) r = -r;
+    return r == 0.0f ? 0.0f : r;  // -0 -> +0
+}
+
+// ------------------------------------------------------- number formats --
+
+__device__ __forceinline__ float bf16_to_f32(uint32_t h) { return __uint_as_float(h << 16); }
+
+// FP8 E4M3 "fn" code -> FP32 (exact): sign, 4-bit exponent with bias 7,
+// 3-bit mantissa, subnormals for a zero exponent field.  The NaN code is
+// rejected when an index is loaded.
+__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
+    uint32_t s = (c & 0x80u) << 24;
+    uint32_t e = (c >> 3) & 0xFu;
+    uint32_t m = c & 7u;
+    if (e == 0) return __uint_as_float(s | __float_as_uint(__uint2float_rn(m) * 0.001953125f));
+    return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
+}
+
+// ------------------------------------------------------------------ keys --
+// A candidate is a 64-bit key: the FP32 distance mapped to an order-preserving
+// unsigned integer in the high word, (id << 1 | checked) in the low word, so
+// that integer order is (distance, id) order.
+
+__device__ __forceinline__ uint32_t orderable(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float from_orderable(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__device__ __forceinline__ uint64_t make_key(float dist, int32_t id) {
+    return (uint64_t(orderable(dist)) << 32) | (uint64_t(uint32_t(id)) << 1);
+}
+
+__device__ __forceinline__ int32_t key_id(uint64_t k) { return int32_t(uint32_t(k) >> 1); }
+__device__ __forceinline__ float key_dist(uint64_t k) { return from_orderable(uint32_t(k >> 32)); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+// Ascending bitonic sort of one key per lane across the warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t o = __shfl_xor_sync(kFull, v, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            v = (lower == up) ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+// ---------------------------------------------------------- visited hash --
+// Exact open-addressing set of node ids in shared memory (linear probing,
+// multiplicative hashing).  When max_probe slots are all taken by other ids
+// the insert fails and the id is treated as unvisited; the candidate merge
+// then drops it if it is already in the list.  That keeps results exactly
+// those of an unbounded visited set: a re-computed node that is not in the
+// list was cut earlier, when the list was full and its worst key was lower,
+// and the worst key of a full list never rises, so it is cut again.
+
+__device__ __forceinline__ void hash_clear(uint32_t* tab, int log2h, int lane) {
+    uint4* t4 = reinterpret_cast<uint4*>(tab);
+    const int n4 = (1 << log2h) >> 2;
+    for (int i = lane; i < n4; i += 32) t4[i] = make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty);
+}
+
+// true if key was absent (now inserted, or not recordable); false if present.
+__device__ __forceinline__ bool hash_insert(uint32_t* tab, int log2h, uint32_t key, int& overflow) {
+    const uint32_t mask = (1u << log2h) - 1u;
+    uint32_t h = (key * 2654435761u) >> (32 - log2h);
+    volatile uint32_t* vt = tab;
+#pragma unroll 1
+    for (int p = 0; p < 32; ++p) {
+        uint32_t s = (h + uint32_t(p)) & mask;
+        uint32_t cur = vt[s];
+        if (cur == key) return false;
+        if (cur == kSlotEmpty) {
+            uint32_t old = atomicCAS(&tab[s], kSlotEmpty, key);
+            if (old == kSlotEmpty) return true;
+            if (old == key) return false;
+        }
+    }
+    overflow += 1;
+    return true;
+}
+
+// ------------------------------------------------------------- cp.async --
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+}  // namespace pilot

@@ -1,0 +1,67 @@
+// kernels.h -- launch interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pilot {
+
+// Device-resident index (library-owned).  Rows are padded with zeros to a
+// multiple of 128 bytes so that eight lanes cover one 128-byte line.
+struct DevIndex {
+    int64_t n, d, dp, n_sub, n_entry;
+    int R, R_sub;
+    int metric;          // 0 L2, 1 IP
+    int red_dtype;       // 0 f32, 1 bf16, 2 fp8
+    int d_pad;           // full row length in floats
+    int dp_pad;          // reduced row length in elements
+    int full_row_bytes;  // d_pad * 4
+    int red_row_bytes;   // dp_pad * element size
+    int qp_pad;          // projected-query row length in floats (multiple of 64)
+    const int32_t* graph;      // n x R original ids
+    const int32_t* sub_adj;    // n_sub x R_sub compact ids
+    const int32_t* sub2full;   // n_sub
+    const int32_t* full2sub;   // n (-1 for unsampled)
+    const void* red;           // n_sub x dp_pad
+    const float* red_scales;   // n_sub (fp8) or null
+    const float* full;         // n x d_pad
+    const float2* basis;       // d x qp_pad, (hi, lo) FP32 pair of each FP64 basis value
+    const int32_t* entry;      // n_entry compact ids
+    const float* entry_f32;    // n_entry x qp_pad, exact decoded reduced rows of the entries
+    const float* entry_norm2;  // n_entry, ||e||^2 (FP32 of the FP64 value)
+    float entry_max_norm;      // max ||e||
+};
+
+struct SearchConfig {
+    int k, ef;
+    int stage1, stage2_expansions, stage3, use_fes;
+    int hash_log2;
+    int warps_per_block;
+    int fes_T;
+    int stage_bytes;     // per-warp row staging buffer
+};
+
+// Per-call device buffers.
+struct SearchIO {
+    const float* queries;      // nq x d (caller layout)
+    int64_t nq;
+    float* q_pad;              // nq x d_pad
+    float* qp;                 // nq x qp_pad
+    int32_t* fes_pos;          // nq x fes_T entry positions
+    double* fes_lb;            // nq lower bound on excluded entries' distances
+    int32_t* out_ids;          // nq x k
+    float* out_dists;          // nq x k
+    int32_t* counters;         // nq x 8 or null
+    int32_t* bad_query;        // nq flags (non-finite input)
+    int32_t* status;           // [0] non-finite queries, [1] next query, [2] hash overflows,
+                               // [3] FES fallbacks, [4] expansion-cap hits
+};
+
+cudaError_t launch_project(const DevIndex& ix, const SearchIO& io, cudaStream_t st);
+cudaError_t launch_fes_scores(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st);
+cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
+                          int num_sms);
+size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
+int search_blocks_per_sm(const DevIndex& ix, const SearchConfig& cfg);
+
+}  // namespace pilot

@@ -1,0 +1,500 @@
+// pilot_api.cu -- the C ABI (include/pilot.h): index loading and validation,
+// per-call workspace, and the launch sequence of a search.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/pilot.h"
+#include "kernels.h"
+
+using namespace pilot;
+
+namespace {
+
+thread_local std::string g_error;
+
+pilot_status fail(pilot_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t e__ = (expr);                                                                   \
+        if (e__ != cudaSuccess)                                                                     \
+            return fail(e__ == cudaErrorMemoryAllocation ? PILOT_ENOMEM : PILOT_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e__), __FILE__, __LINE__);                        \
+    } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+double decode_e4m3_host(uint8_t c) {
+    int e = (c >> 3) & 0xF, m = c & 7;
+    double v = e == 0 ? std::ldexp(double(m), -9) : std::ldexp(1.0 + m / 8.0, e - 7);
+    return (c & 0x80) ? -v : v;
+}
+
+double decode_bf16_host(uint16_t h) {
+    uint32_t b = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+}  // namespace
+
+struct pilot_index {
+    DevIndex dev{};
+    std::vector<void*> allocs;
+    int device = 0;
+    int num_sms = 0;
+    std::mutex mu;
+    // per-call workspace (grow-only)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int32_t* status_host = nullptr;   // pinned
+    size_t device_bytes = 0;
+
+    ~pilot_index() {
+        for (void* p : allocs) cudaFree(p);
+        if (ws) cudaFree(ws);
+        if (status_host) cudaFreeHost(status_host);
+    }
+
+    template <class T>
+    pilot_status upload(const T* host, size_t count, const T** out) {
+        void* p = nullptr;
+        size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        CUDA_TRY(cudaMalloc(&p, bytes));
+        allocs.push_back(p);
+        device_bytes += bytes;
+        if (count) CUDA_TRY(cudaMemcpy(p, host, count * sizeof(T), cudaMemcpyHostToDevice));
+        *out = static_cast<const T*>(p);
+        return PILOT_OK;
+    }
+
+    // rows x width elements of esize bytes into rows x pitch_bytes, zero padded
+    pilot_status upload_rows(const void* host, int64_t rows, size_t width_bytes, size_t pitch_bytes,
+                             const void** out) {
+        void* p = nullptr;
+        size_t bytes = std::max<size_t>(size_t(rows) * pitch_bytes, 16);
+        CUDA_TRY(cudaMalloc(&p, bytes));
+        allocs.push_back(p);
+        device_bytes += bytes;
+        if (pitch_bytes != width_bytes) CUDA_TRY(cudaMemset(p, 0, bytes));
+        if (rows)
+            CUDA_TRY(cudaMemcpy2D(p, pitch_bytes, host, width_bytes, width_bytes, size_t(rows),
+                                  cudaMemcpyHostToDevice));
+        *out = p;
+        return PILOT_OK;
+    }
+};
+
+extern "C" {
+
+const char* pilot_last_error(void) { return g_error.c_str(); }
+
+int pilot_abi_version(void) { return 1; }
+
+void pilot_search_options_default(pilot_search_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->stage1 = 1;
+    opt->stage2_expansions = 2;
+    opt->stage3 = 1;
+    opt->use_fes = 1;
+}
+
+void pilot_index_free(pilot_index* index) { delete index; }
+
+pilot_status pilot_index_info(const pilot_index* index, int64_t* n, int64_t* d, int64_t* dp, int64_t* n_sub,
+                              int64_t* device_bytes) {
+    if (!index) return fail(PILOT_EINVAL, "index is NULL");
+    if (n) *n = index->dev.n;
+    if (d) *d = index->dev.d;
+    if (dp) *dp = index->dev.dp;
+    if (n_sub) *n_sub = index->dev.n_sub;
+    if (device_bytes) *device_bytes = int64_t(index->device_bytes);
+    return PILOT_OK;
+}
+
+static pilot_status validate_rows(const int32_t* adj, int64_t rows, int64_t width, int64_t n, const uint8_t* mask,
+                                  bool sub, const char* what) {
+    std::vector<int64_t> stamp(size_t(n), -1);
+    for (int64_t r = 0; r < rows; ++r) {
+        const int32_t* row = adj + r * width;
+        for (int64_t j = 0; j < width; ++j) {
+            int32_t v = row[j];
+            if (v < -1 || v >= n) return fail(PILOT_EINVAL, "%s row %lld holds id %d outside [-1, n)", what,
+                                              (long long)r, v);
+            if (v < 0) continue;
+            if (sub && !mask[r]) return fail(PILOT_EINVAL, "%s row %lld of an unsampled node is not empty", what,
+                                             (long long)r);
+            if (sub && !mask[v]) return fail(PILOT_EINVAL, "%s edge %lld -> %d reaches an unsampled node", what,
+                                             (long long)r, v);
+            if (stamp[v] == r) return fail(PILOT_EINVAL, "%s row %lld repeats id %d", what, (long long)r, v);
+            stamp[v] = r;
+        }
+    }
+    return PILOT_OK;
+}
+
+pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
+    if (!dsc || !out) return fail(PILOT_EINVAL, "desc and out must not be NULL");
+    *out = nullptr;
+    const pilot_index_desc& D = *dsc;
+    if (D.n < 1 || D.n >= (int64_t(1) << 31)) return fail(PILOT_EINVAL, "n = %lld out of range", (long long)D.n);
+    if (D.d < 1 || D.d > 4096) return fail(PILOT_EINVAL, "d = %lld out of range [1, 4096]", (long long)D.d);
+    if (D.dp < 1 || D.dp > D.d || D.dp > 128)
+        return fail(PILOT_EINVAL, "dp = %lld must be in [1, min(d, 128)]", (long long)D.dp);
+    if (D.R < 1 || D.R > PILOT_MAX_DEGREE || D.R_sub < 1 || D.R_sub > PILOT_MAX_DEGREE)
+        return fail(PILOT_EINVAL, "R and R_sub must be in [1, %d]", PILOT_MAX_DEGREE);
+    if (D.n_entry < 1) return fail(PILOT_EINVAL, "n_entry must be >= 1");
+    if (D.metric != PILOT_METRIC_L2 && D.metric != PILOT_METRIC_IP) return fail(PILOT_EINVAL, "bad metric");
+    if (D.reduced_dtype < 0 || D.reduced_dtype > 2) return fail(PILOT_EINVAL, "bad reduced_dtype");
+    if (!D.graph || !D.subgraph_mask || !D.subgraph || !D.svd_basis || !D.reduced_vecs || !D.full_vecs ||
+        !D.entry_ids)
+        return fail(PILOT_EINVAL, "a required array is NULL");
+    if ((D.reduced_dtype == PILOT_REDUCED_FP8_E4M3) != (D.reduced_scales != nullptr))
+        return fail(PILOT_EINVAL, "reduced_scales must be given exactly for FP8 rows");
+
+    const int64_t n = D.n, d = D.d, dp = D.dp;
+    std::vector<int32_t> sub2full, full2sub(size_t(n), -1);
+    for (int64_t v = 0; v < n; ++v) {
+        if (D.subgraph_mask[v] > 1) return fail(PILOT_EINVAL, "subgraph_mask must hold 0 or 1");
+        if (D.subgraph_mask[v]) {
+            full2sub[size_t(v)] = int32_t(sub2full.size());
+            sub2full.push_back(int32_t(v));
+        }
+    }
+    const int64_t n_sub = int64_t(sub2full.size());
+    if (n_sub < 1) return fail(PILOT_EINVAL, "the subgraph samples no node");
+    pilot_status s;
+    if ((s = validate_rows(D.graph, n, D.R, n, nullptr, false, "graph")) != PILOT_OK) return s;
+    if ((s = validate_rows(D.subgraph, n, D.R_sub, n, D.subgraph_mask, true, "subgraph")) != PILOT_OK) return s;
+    for (int64_t e = 0; e < D.n_entry; ++e) {
+        int32_t v = D.entry_ids[e];
+        if (v < 0 || v >= n || !D.subgraph_mask[v])
+            return fail(PILOT_EINVAL, "entry %lld (id %d) is not a sampled node", (long long)e, v);
+    }
+    for (int64_t i = 0; i < n * d; ++i)
+        if (!std::isfinite(D.full_vecs[i])) return fail(PILOT_EINVAL, "full_vecs holds a non-finite value");
+    for (int64_t i = 0; i < d * dp; ++i)
+        if (!std::isfinite(D.svd_basis[i])) return fail(PILOT_EINVAL, "svd_basis holds a non-finite value");
+
+    const int esize = D.reduced_dtype == 0 ? 4 : (D.reduced_dtype == 1 ? 2 : 1);
+    auto red_value = [&](int64_t r, int64_t c) -> double {
+        int64_t at = r * dp + c;
+        if (D.reduced_dtype == 0) return double(static_cast<const float*>(D.reduced_vecs)[at]);
+        if (D.reduced_dtype == 1) return decode_bf16_host(static_cast<const uint16_t*>(D.reduced_vecs)[at]);
+        return decode_e4m3_host(static_cast<const uint8_t*>(D.reduced_vecs)[at]) * double(D.reduced_scales[r]);
+    };
+    if (D.reduced_dtype == 2) {
+        const uint8_t* codes = static_cast<const uint8_t*>(D.reduced_vecs);
+        for (int64_t i = 0; i < n_sub * dp; ++i)
+            if ((codes[i] & 0x7F) == 0x7F) return fail(PILOT_EINVAL, "reduced_vecs holds an FP8 NaN code");
+        for (int64_t r = 0; r < n_sub; ++r)
+            if (!(D.reduced_scales[r] > 0.0f) || !std::isfinite(D.reduced_scales[r]))
+                return fail(PILOT_EINVAL, "reduced_scales must be finite and > 0");
+    } else {
+        for (int64_t r = 0; r < n_sub; ++r)
+            for (int64_t c = 0; c < dp; ++c)
+                if (!std::isfinite(red_value(r, c))) return fail(PILOT_EINVAL, "reduced_vecs holds a non-finite value");
+    }
+
+    auto* ix = new pilot_index();
+    std::unique_ptr<pilot_index> guard(ix);
+    CUDA_TRY(cudaGetDevice(&ix->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, ix->device));
+    DevIndex& X = ix->dev;
+    X.n = n;
+    X.d = d;
+    X.dp = dp;
+    X.n_sub = n_sub;
+    X.n_entry = D.n_entry;
+    X.R = int(D.R);
+    X.R_sub = int(D.R_sub);
+    X.metric = D.metric;
+    X.red_dtype = D.reduced_dtype;
+    X.d_pad = round_up(int(d), 32);
+    X.full_row_bytes = X.d_pad * 4;
+    X.red_row_bytes = round_up(int(dp) * esize, 128);
+    X.dp_pad = X.red_row_bytes / esize;
+    X.qp_pad = std::max(round_up(int(dp), 64), X.dp_pad);
+
+    // compact subgraph (ids of sampled rows in ascending original order)
+    std::vector<int32_t> sub_adj(size_t(n_sub * D.R_sub));
+    for (int64_t c = 0; c < n_sub; ++c)
+        for (int64_t j = 0; j < D.R_sub; ++j) {
+            int32_t v = D.subgraph[int64_t(sub2full[c]) * D.R_sub + j];
+            sub_adj[size_t(c * D.R_sub + j)] = v < 0 ? -1 : full2sub[size_t(v)];
+        }
+    // basis as (hi, lo) FP32 pairs, zero beyond dp
+    std::vector<float2> basis(size_t(d * X.qp_pad), make_float2(0.f, 0.f));
+    for (int64_t j = 0; j < d; ++j)
+        for (int64_t c = 0; c < dp; ++c) {
+            double v = D.svd_basis[j * dp + c];
+            float hi = float(v);
+            float lo = float(v - double(hi));
+            basis[size_t(j * X.qp_pad + c)] = make_float2(hi, lo);
+        }
+    // entries: compact ids, decoded rows, norms
+    std::vector<int32_t> entry(size_t(D.n_entry));
+    std::vector<float> entry_f32(size_t(D.n_entry * X.qp_pad), 0.f), entry_n2(size_t(D.n_entry));
+    double emax = 0.0;
+    for (int64_t e = 0; e < D.n_entry; ++e) {
+        int32_t c = full2sub[size_t(D.entry_ids[e])];
+        entry[size_t(e)] = c;
+        double nn = 0.0;
+        for (int64_t k = 0; k < dp; ++k) {
+            double v = red_value(c, k);
+            entry_f32[size_t(e * X.qp_pad + k)] = float(v);
+            nn += v * v;
+        }
+        entry_n2[size_t(e)] = float(nn);
+        emax = std::max(emax, std::sqrt(nn));
+    }
+    X.entry_max_norm = float(emax * (1.0 + 1e-6));
+
+    if ((s = ix->upload(D.graph, size_t(n * D.R), &X.graph)) != PILOT_OK) return s;
+    if ((s = ix->upload(sub_adj.data(), sub_adj.size(), &X.sub_adj)) != PILOT_OK) return s;
+    if ((s = ix->upload(sub2full.data(), sub2full.size(), &X.sub2full)) != PILOT_OK) return s;
+    if ((s = ix->upload(full2sub.data(), full2sub.size(), &X.full2sub)) != PILOT_OK) return s;
+    if ((s = ix->upload(basis.data(), basis.size(), &X.basis)) != PILOT_OK) return s;
+    if ((s = ix->upload(entry.data(), entry.size(), &X.entry)) != PILOT_OK) return s;
+    if ((s = ix->upload(entry_f32.data(), entry_f32.size(), &X.entry_f32)) != PILOT_OK) return s;
+    if ((s = ix->upload(entry_n2.data(), entry_n2.size(), &X.entry_norm2)) != PILOT_OK) return s;
+    X.red_scales = nullptr;
+    if (D.reduced_dtype == 2)
+        if ((s = ix->upload(D.reduced_scales, size_t(n_sub), &X.red_scales)) != PILOT_OK) return s;
+    const void* p = nullptr;
+    if ((s = ix->upload_rows(D.reduced_vecs, n_sub, size_t(dp * esize), size_t(X.red_row_bytes), &p)) != PILOT_OK)
+        return s;
+    X.red = p;
+    if ((s = ix->upload_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) return s;
+    X.full = static_cast<const float*>(p);
+    CUDA_TRY(cudaMallocHost(&ix->status_host, 8 * sizeof(int32_t)));
+    *out = guard.release();
+    return PILOT_OK;
+}
+
+
+static uint64_t checksum64(const std::vector<char>& b) {
+    uint64_t sum = 0;
+    size_t nw = (b.size() + 7) / 8;
+    for (size_t i = 0; i < nw; ++i) {
+        uint64_t w = 0;
+        size_t take = std::min<size_t>(8, b.size() - i * 8);
+        std::memcpy(&w, b.data() + i * 8, take);   // little-endian host
+        sum += w * (2 * uint64_t(i) + 1);
+    }
+    return sum;
+}
+
+pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** out) {
+    if (!dir || !out) return fail(PILOT_EINVAL, "dir and out must not be NULL");
+    if (flags != 0) return fail(PILOT_EINVAL, "flags must be 0");
+    *out = nullptr;
+    const std::string root(dir);
+    std::ifstream hdr(root + "/pilot_index.txt");
+    if (!hdr) return fail(PILOT_EIO, "cannot open %s/pilot_index.txt", dir);
+    std::string line;
+    if (!std::getline(hdr, line) || line != "pilot-index 1") return fail(PILOT_EFORMAT, "bad header line");
+    std::map<std::string, int64_t> meta;
+    std::map<std::string, std::vector<char>> arrays;
+    while (std::getline(hdr, line)) {
+        if (line.empty()) continue;
+        std::istringstream ls(line);
+        std::string key;
+        ls >> key;
+        if (key == "array") {
+            std::string name, kind, sum_hex;
+            long long bytes = -1;
+            ls >> name >> kind >> bytes >> sum_hex;
+            if (!ls || bytes < 0) return fail(PILOT_EFORMAT, "bad array line: %s", line.c_str());
+            std::ifstream f(root + "/" + name + ".bin", std::ios::binary | std::ios::ate);
+            if (!f) return fail(PILOT_EIO, "cannot open %s.bin", name.c_str());
+            if (int64_t(f.tellg()) != bytes) return fail(PILOT_EFORMAT, "%s.bin has the wrong size", name.c_str());
+            f.seekg(0);
+            std::vector<char> buf(static_cast<size_t>(bytes));
+            if (bytes && !f.read(buf.data(), bytes)) return fail(PILOT_EIO, "cannot read %s.bin", name.c_str());
+            if (checksum64(buf) != std::stoull(sum_hex, nullptr, 16))
+                return fail(PILOT_EFORMAT, "%s.bin fails its checksum", name.c_str());
+            arrays[name] = std::move(buf);
+        } else {
+            long long v;
+            if (!(ls >> v)) return fail(PILOT_EFORMAT, "bad line: %s", line.c_str());
+            meta[key] = v;
+        }
+    }
+    for (const char* k : {"n", "d", "dp", "R", "R_sub", "n_sub", "n_entry", "metric", "reduced_dtype"})
+        if (!meta.count(k)) return fail(PILOT_EFORMAT, "missing key %s", k);
+    const int64_t n = meta["n"], d = meta["d"], dp = meta["dp"], R = meta["R"], Rs = meta["R_sub"];
+    const int64_t ns = meta["n_sub"], ne = meta["n_entry"];
+    const int dt = int(meta["reduced_dtype"]);
+    const int es = dt == 0 ? 4 : (dt == 1 ? 2 : 1);
+    struct Need { const char* name; int64_t bytes; };
+    std::vector<Need> need = {{"graph", n * R * 4}, {"subgraph_mask", n}, {"subgraph", n * Rs * 4},
+                              {"svd_basis", 0}, {"basis", d * dp * 8}, {"reduced", ns * dp * es},
+                              {"full", n * d * 4}, {"entry_ids", ne * 4}};
+    for (auto& nd : need) {
+        if (nd.bytes == 0) continue;
+        auto it = arrays.find(nd.name);
+        if (it == arrays.end()) return fail(PILOT_EFORMAT, "missing array %s", nd.name);
+        if (int64_t(it->second.size()) != nd.bytes) return fail(PILOT_EFORMAT, "array %s has the wrong size", nd.name);
+    }
+    if (dt == 2 && (!arrays.count("reduced_scales") || int64_t(arrays["reduced_scales"].size()) != ns * 4))
+        return fail(PILOT_EFORMAT, "missing or short reduced_scales");
+    const uint8_t* mask = reinterpret_cast<const uint8_t*>(arrays["subgraph_mask"].data());
+    int64_t cnt = 0;
+    for (int64_t v = 0; v < n; ++v) cnt += mask[v] != 0;
+    if (cnt != ns) return fail(PILOT_EFORMAT, "n_sub does not match subgraph_mask");
+    pilot_index_desc D{};
+    D.n = n; D.d = d; D.dp = dp; D.R = R; D.R_sub = Rs; D.n_entry = ne;
+    D.metric = int32_t(meta["metric"]);
+    D.reduced_dtype = dt;
+    D.graph = reinterpret_cast<const int32_t*>(arrays["graph"].data());
+    D.subgraph_mask = mask;
+    D.subgraph = reinterpret_cast<const int32_t*>(arrays["subgraph"].data());
+    D.svd_basis = reinterpret_cast<const double*>(arrays["basis"].data());
+    D.reduced_vecs = arrays["reduced"].data();
+    D.reduced_scales = dt == 2 ? reinterpret_cast<const float*>(arrays["reduced_scales"].data()) : nullptr;
+    D.full_vecs = reinterpret_cast<const float*>(arrays["full"].data());
+    D.entry_ids = reinterpret_cast<const int32_t*>(arrays["entry_ids"].data());
+    return pilot_index_load(&D, out);
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, int k, int ef, int32_t* out_ids,
+                             float* out_dists, void* stream, const pilot_search_options* opt_in) {
+    if (!ix) return fail(PILOT_EINVAL, "index is NULL");
+    if (nq < 0) return fail(PILOT_EINVAL, "nq < 0");
+    if (k < 1) return fail(PILOT_EINVAL, "k = %d < 1", k);
+    if (ef < k) return fail(PILOT_EINVAL, "ef = %d < k = %d", ef, k);
+    if (ef > PILOT_MAX_EF) return fail(PILOT_EINVAL, "ef = %d > %d", ef, PILOT_MAX_EF);
+    if (nq > 0 && (!queries || !out_ids || !out_dists)) return fail(PILOT_EINVAL, "NULL query or output buffer");
+    pilot_search_options opt;
+    pilot_search_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.stage2_expansions < 0) return fail(PILOT_EINVAL, "stage2_expansions < 0");
+    if (nq == 0) return PILOT_OK;
+    std::lock_guard<std::mutex> lock(ix->mu);
+    CUDA_TRY(cudaSetDevice(ix->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const DevIndex& X = ix->dev;
+
+    SearchConfig cfg{};
+    cfg.k = k;
+    cfg.ef = ef;
+    cfg.stage1 = opt.stage1 != 0;
+    cfg.stage2_expansions = opt.stage2_expansions;
+    cfg.stage3 = opt.stage3 != 0;
+    cfg.use_fes = opt.use_fes != 0;
+    cfg.fes_T = 8;
+    cfg.warps_per_block = opt.warps_per_block > 0 ? std::min(opt.warps_per_block, 8) : 4;
+    int hl = opt.hash_log2;
+    if (hl <= 0) {
+        hl = 10;
+        while ((1 << hl) < 8 * ef && hl < 13) ++hl;
+    }
+    if (hl < 5 || hl > 16) return fail(PILOT_EINVAL, "hash_log2 = %d out of [5, 16]", hl);
+    cfg.hash_log2 = hl;
+    int stage = std::max(4 * X.full_row_bytes, 4 * X.red_row_bytes);
+    stage = std::max(stage, std::min(32 * X.full_row_bytes, 16384));
+    stage = std::max(stage, 32 * X.red_row_bytes);
+    cfg.stage_bytes = stage;
+
+    const bool q_dev = is_device_ptr(queries);
+    const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);
+    const bool cnt_dev = opt.counters ? is_device_ptr(opt.counters) : true;
+
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_status = take(8 * 4);
+    const size_t o_qpad = take(size_t(nq) * X.d_pad * 4);
+    const size_t o_qp = take(size_t(nq) * X.qp_pad * 4);
+    const size_t o_pos = take(size_t(nq) * cfg.fes_T * 4);
+    const size_t o_lb = take(size_t(nq) * 8);
+    const size_t o_bad = take(size_t(nq) * 4);
+    const size_t o_q = q_dev ? 0 : take(size_t(nq) * X.d * 4);
+    const size_t o_ids = ids_dev ? 0 : take(size_t(nq) * k * 4);
+    const size_t o_dists = dists_dev ? 0 : take(size_t(nq) * k * 4);
+    const size_t o_cnt = (opt.counters && !cnt_dev) ? take(size_t(nq) * 8 * 4) : 0;
+    if (off > ix->ws_bytes) {
+        if (ix->ws) cudaFree(ix->ws);
+        ix->ws = nullptr;
+        ix->ws_bytes = 0;
+        CUDA_TRY(cudaMalloc(&ix->ws, off));
+        ix->ws_bytes = off;
+    }
+    char* ws = static_cast<char*>(ix->ws);
+    SearchIO io{};
+    io.nq = nq;
+    io.status = reinterpret_cast<int32_t*>(ws + o_status);
+    io.q_pad = reinterpret_cast<float*>(ws + o_qpad);
+    io.qp = reinterpret_cast<float*>(ws + o_qp);
+    io.fes_pos = reinterpret_cast<int32_t*>(ws + o_pos);
+    io.fes_lb = reinterpret_cast<double*>(ws + o_lb);
+    io.bad_query = reinterpret_cast<int32_t*>(ws + o_bad);
+    io.queries = q_dev ? queries : reinterpret_cast<const float*>(ws + o_q);
+    io.out_ids = ids_dev ? out_ids : reinterpret_cast<int32_t*>(ws + o_ids);
+    io.out_dists = dists_dev ? out_dists : reinterpret_cast<float*>(ws + o_dists);
+    io.counters = opt.counters ? (cnt_dev ? opt.counters : reinterpret_cast<int32_t*>(ws + o_cnt)) : nullptr;
+
+    CUDA_TRY(cudaMemsetAsync(io.status, 0, 8 * 4, st));
+    if (!q_dev)
+        CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(io.queries), queries, size_t(nq) * X.d * 4,
+                                 cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_project(X, io, st));
+    if (cfg.use_fes) CUDA_TRY(launch_fes_scores(X, cfg, io, st));
+    CUDA_TRY(launch_search(X, cfg, io, st, ix->num_sms));
+    if (!ids_dev) CUDA_TRY(cudaMemcpyAsync(out_ids, io.out_ids, size_t(nq) * k * 4, cudaMemcpyDeviceToHost, st));
+    if (!dists_dev)
+        CUDA_TRY(cudaMemcpyAsync(out_dists, io.out_dists, size_t(nq) * k * 4, cudaMemcpyDeviceToHost, st));
+    if (opt.counters && !cnt_dev)
+        CUDA_TRY(cudaMemcpyAsync(opt.counters, io.counters, size_t(nq) * 8 * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(ix->status_host, io.status, 8 * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const int32_t* S = ix->status_host;
+    if (S[4]) return fail(PILOT_ECUDA, "%d queries hit the expansion cap", S[4]);
+    if (S[0]) return fail(PILOT_EINVAL, "%d queries hold NaN or infinity (their results are -1 / +inf)", S[0]);
+    return PILOT_OK;
+}
+
+pilot_status pilot_search(pilot_index* index, const float* queries, int64_t nq, int k, int ef, int32_t* out_ids,
+                          float* out_dists, void* stream) {
+    return pilot_search_ex(index, queries, nq, k, ef, out_ids, out_dists, stream, nullptr);
+}
+
+}  // extern "C"

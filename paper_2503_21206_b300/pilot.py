@@ -1,0 +1,194 @@
+"""Thin ctypes binding of libpilot (include/pilot.h): argument marshalling only.
+
+Every step of a search runs in the library's CUDA kernels.  Arrays may be
+numpy arrays (host memory) or torch tensors (host or CUDA); torch is used only
+to hold device memory and streams.  If libpilot.so is missing this module
+raises on import: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpilot.so")
+
+PILOT_OK, PILOT_EINVAL, PILOT_ENOMEM, PILOT_ECUDA, PILOT_EIO, PILOT_ETIMEOUT, PILOT_EBUSY, PILOT_EFORMAT = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EIO", "ETIMEOUT", "EBUSY", "EFORMAT"]
+METRIC_L2, METRIC_IP = 0, 1
+REDUCED_CODES = {"f32": 0, "bf16": 1, "fp8": 2}
+PILOT_MAX_EF = 512
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpilot.so not built ({LIB_PATH}); run paper_2503_21206_b300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class PilotError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"PILOT_{name}: {message}")
+
+
+class pilot_index_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("dp", ctypes.c_int64), ("R", ctypes.c_int64),
+                ("R_sub", ctypes.c_int64), ("n_entry", ctypes.c_int64), ("metric", ctypes.c_int32),
+                ("reduced_dtype", ctypes.c_int32), ("graph", ctypes.c_void_p), ("subgraph_mask", ctypes.c_void_p),
+                ("subgraph", ctypes.c_void_p), ("svd_basis", ctypes.c_void_p), ("reduced_vecs", ctypes.c_void_p),
+                ("reduced_scales", ctypes.c_void_p), ("full_vecs", ctypes.c_void_p), ("entry_ids", ctypes.c_void_p)]
+
+
+class pilot_search_options(ctypes.Structure):
+    _fields_ = [("stage1", ctypes.c_int32), ("stage2_expansions", ctypes.c_int32), ("stage3", ctypes.c_int32),
+                ("use_fes", ctypes.c_int32), ("hash_log2", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("counters", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_lib.pilot_last_error.restype = ctypes.c_char_p
+_lib.pilot_abi_version.restype = ctypes.c_int
+_lib.pilot_index_load.argtypes = [ctypes.POINTER(pilot_index_desc), ctypes.POINTER(_P)]
+_lib.pilot_index_load_files.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_P)]
+_lib.pilot_index_free.argtypes = [_P]
+_lib.pilot_index_free.restype = None
+_lib.pilot_index_info.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int64)] * 5
+_lib.pilot_search_options_default.argtypes = [ctypes.POINTER(pilot_search_options)]
+_lib.pilot_search_options_default.restype = None
+_lib.pilot_search.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+_lib.pilot_search_ex.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                 ctypes.POINTER(pilot_search_options)]
+
+
+def pilot_last_error() -> str:
+    return _lib.pilot_last_error().decode()
+
+
+def pilot_abi_version() -> int:
+    return _lib.pilot_abi_version()
+
+
+def _check(status: int):
+    if status != PILOT_OK:
+        raise PilotError(status, pilot_last_error())
+
+
+def _addr(a):
+    """Raw address of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def pilot_search_options_default() -> pilot_search_options:
+    o = pilot_search_options()
+    _lib.pilot_search_options_default(ctypes.byref(o))
+    return o
+
+
+class PilotIndex:
+    """Owns a pilot_index handle (device memory held by the library)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        vals = [ctypes.c_int64() for _ in range(5)]
+        _check(_lib.pilot_index_info(self._h, *[ctypes.byref(v) for v in vals]))
+        return dict(zip(["n", "d", "dp", "n_sub", "device_bytes"], [v.value for v in vals]))
+
+    def free(self):
+        if self._h:
+            _lib.pilot_index_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, full_vecs, entry_ids, *,
+                     metric: int = METRIC_L2, reduced_dtype: str = "f32", reduced_scales=None) -> PilotIndex:
+    """Copy an index (host numpy arrays, layouts as in pilot.h) to the current device."""
+    arrs = dict(graph=np.ascontiguousarray(graph, np.int32), subgraph_mask=np.ascontiguousarray(subgraph_mask, np.uint8),
+                subgraph=np.ascontiguousarray(subgraph, np.int32),
+                svd_basis=np.ascontiguousarray(svd_basis, np.float64),
+                reduced_vecs=np.ascontiguousarray(reduced_vecs),
+                full_vecs=np.ascontiguousarray(full_vecs, np.float32),
+                entry_ids=np.ascontiguousarray(entry_ids, np.int32))
+    sc = None if reduced_scales is None else np.ascontiguousarray(reduced_scales, np.float32)
+    n, d = arrs["full_vecs"].shape
+    desc = pilot_index_desc(n=n, d=d, dp=arrs["svd_basis"].shape[1], R=arrs["graph"].shape[1],
+                            R_sub=arrs["subgraph"].shape[1], n_entry=arrs["entry_ids"].shape[0], metric=metric,
+                            reduced_dtype=REDUCED_CODES[reduced_dtype], graph=_addr(arrs["graph"]),
+                            subgraph_mask=_addr(arrs["subgraph_mask"]), subgraph=_addr(arrs["subgraph"]),
+                            svd_basis=_addr(arrs["svd_basis"]), reduced_vecs=_addr(arrs["reduced_vecs"]),
+                            reduced_scales=_addr(sc), full_vecs=_addr(arrs["full_vecs"]),
+                            entry_ids=_addr(arrs["entry_ids"]))
+    h = _P()
+    _check(_lib.pilot_index_load(ctypes.byref(desc), ctypes.byref(h)))
+    return PilotIndex(h.value)
+
+
+def load_index_data(idx) -> PilotIndex:
+    """pilot_index_load of an ``index_build.PilotIndexData``."""
+    return pilot_index_load(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, idx.full,
+                            idx.entry_ids, metric=idx.metric, reduced_dtype=idx.reduced_dtype,
+                            reduced_scales=idx.reduced_scales)
+
+
+def pilot_index_load_files(path: str) -> PilotIndex:
+    h = _P()
+    _check(_lib.pilot_index_load_files(path.encode(), 0, ctypes.byref(h)))
+    return PilotIndex(h.value)
+
+
+def pilot_search(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_dists=None, stream=None, *,
+                 options: pilot_search_options | None = None, counters=None):
+    """Top-k search.  ``queries`` is an nq x d float32 numpy array or torch
+    tensor (host or CUDA); outputs default to host numpy arrays.  ``stream``
+    is a torch.cuda.Stream (or raw handle).  Returns (ids, dists)."""
+    nq = int(queries.shape[0])
+    if out_ids is None:
+        out_ids = np.empty((nq, k), np.int32)
+    if out_dists is None:
+        out_dists = np.empty((nq, k), np.float32)
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    if options is None and counters is None:
+        _check(_lib.pilot_search(index.handle, _addr(queries), nq, k, ef, _addr(out_ids), _addr(out_dists), s))
+    else:
+        o = options if options is not None else pilot_search_options_default()
+        o.counters = _addr(counters)
+        _check(_lib.pilot_search_ex(index.handle, _addr(queries), nq, k, ef, _addr(out_ids), _addr(out_dists), s,
+                                    ctypes.byref(o)))
+    return out_ids, out_dists
+
+
+def pilot_search_ex(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_dists=None, stream=None,
+                    options: pilot_search_options | None = None, counters=None):
+    """pilot_search with explicit options (``pilot_search_options``)."""
+    return pilot_search(index, queries, k, ef, out_ids, out_dists, stream,
+                        options=options if options is not None else pilot_search_options_default(),
+                        counters=counters)
+
+
+def pilot_index_info(index: PilotIndex) -> dict:
+    return index.info()
+
+
+def pilot_index_free(index: PilotIndex) -> None:
+    index.free()

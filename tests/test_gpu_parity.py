@@ -1,0 +1,246 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Both sides round each distance once to FP32 and break ties by id, so ids,
+distances and per-stage counters must be identical.  The tolerance the paper's
+reading allows (ties within 1e-5 relative) is kept as the fallback check
+``assert_parity`` reports against when anything differs."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_21206_b300 import index_build, synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def pilot(torch_cuda):
+    from paper_2503_21206_b300 import build
+    build.build()
+    from paper_2503_21206_b300 import pilot as p
+    return p
+
+
+def oracle_index(idx):
+    dt = {"f32": oracle.DTYPE_F32, "bf16": oracle.DTYPE_BF16, "fp8": oracle.DTYPE_FP8}[idx.reduced_dtype]
+    return oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, dt,
+                              idx.reduced_scales, idx.full, idx.entry_ids, idx.metric)
+
+
+def gpu_search(pilot, torch, gidx, Q, k, ef, device=True, **opts):
+    o = pilot.pilot_search_options_default()
+    for key, v in opts.items():
+        setattr(o, key, int(v))
+    nq = len(Q)
+    if device:
+        q = torch.from_numpy(Q).cuda()
+        ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+        dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        cnt = torch.empty((nq, 8), dtype=torch.int32, device="cuda")
+        pilot.pilot_search_ex(gidx, q, k, ef, ids, dists, options=o, counters=cnt)
+        torch.cuda.synchronize()
+        return ids.cpu().numpy(), dists.cpu().numpy(), cnt.cpu().numpy()
+    cnt = np.empty((nq, 8), np.int32)
+    ids, dists = pilot.pilot_search_ex(gidx, np.ascontiguousarray(Q), k, ef, options=o, counters=cnt)
+    return ids, dists, cnt
+
+
+def assert_parity(ids, dists, ref_ids, ref_dists, rel_tie=1e-5):
+    """ids equal except where the two distances tie within rel_tie."""
+    bad = []
+    for i in range(ids.shape[0]):
+        if np.array_equal(ids[i], ref_ids[i]) and np.array_equal(dists[i], ref_dists[i]):
+            continue
+        for j in range(ids.shape[1]):
+            if ids[i, j] == ref_ids[i, j]:
+                continue
+            a, b = float(dists[i, j]), float(ref_dists[i, j])
+            if not (np.isfinite(a) and np.isfinite(b) and abs(a - b) <= rel_tie * max(abs(a), abs(b))):
+                bad.append((i, j, int(ids[i, j]), int(ref_ids[i, j]), a, b))
+    assert not bad, f"{len(bad)} mismatches, first: {bad[:5]}"
+
+
+@pytest.fixture(scope="module")
+def c1(pilot):
+    w = synth.WORKLOADS["c1_mixture_20k_d96"]
+    idx, Q, red32, V = index_build.build_workload(w)
+    return w, idx, Q, red32, pilot.load_index_data(idx)
+
+
+def test_c1_full_parity(c1, pilot, torch_cuda):
+    """The tiny parity workload at its stated size (N=20k, 200 queries, k=10,
+    ef=64): ids, distances and per-stage counters identical."""
+    w, idx, Q, _, g = c1
+    ref = oracle.search(oracle_index(idx), Q, w.k, 64)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, w.k, 64)
+    assert_parity(ids, dists, ref["ids"], ref["dists"])
+    assert np.array_equal(ids, ref["ids"])
+    assert np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+@pytest.mark.parametrize("k, ef", [(1, 1), (1, 32), (10, 10), (10, 33), (32, 128), (100, 512)])
+def test_c1_k_ef_grid(c1, pilot, torch_cuda, k, ef):
+    w, idx, Q, _, g = c1
+    Qs = Q[:37]
+    ref = oracle.search(oracle_index(idx), Qs, k, ef)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Qs, k, ef)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+@pytest.mark.parametrize("opts", [dict(stage1=0), dict(stage2_expansions=0), dict(stage3=0), dict(use_fes=0),
+                                  dict(stage1=0, stage2_expansions=0), dict(stage2_expansions=5)])
+def test_stage_switches(c1, pilot, torch_cuda, opts):
+    w, idx, Q, _, g = c1
+    Qs = Q[:40]
+    oopts = dict(stage1=bool(opts.get("stage1", 1)), stage2_expansions=opts.get("stage2_expansions", 2),
+                 stage3=bool(opts.get("stage3", 1)), use_fes=bool(opts.get("use_fes", 1)))
+    ref = oracle.search(oracle_index(idx), Qs, 10, 64, **oopts)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Qs, 10, 64, **opts)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+def test_hash_overflow_keeps_results(c1, pilot, torch_cuda):
+    """A 32-slot visited table overflows constantly; results must not change
+    (the candidate merge drops re-computed nodes), only the work grows."""
+    w, idx, Q, _, g = c1
+    ref = oracle.search(oracle_index(idx), Q[:50], 10, 128)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q[:50], 10, 128, hash_log2=5)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.all(cnt[:, [0, 2, 4, 6, 7]] == ref["counters"][:, [0, 2, 4, 6, 7]])
+    assert np.all(cnt[:, [1, 3, 5]] >= ref["counters"][:, [1, 3, 5]])
+
+
+def test_host_and_device_buffers_agree(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    a = gpu_search(pilot, torch_cuda, g, Q[:64], 10, 64, device=True)
+    b = gpu_search(pilot, torch_cuda, g, Q[:64], 10, 64, device=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_ragged_and_empty_batches(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    for nq in (0, 1, 31, 33, 129):
+        Qs = np.ascontiguousarray(Q[:nq])
+        ids, dists, _ = gpu_search(pilot, torch_cuda, g, Qs, 10, 64, device=False)
+        if nq:
+            ref = oracle.search(oracle_index(idx), Qs, 10, 64)
+            assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+
+
+def test_nonfinite_query_rejected_others_answered(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    Qs = Q[:8].copy()
+    Qs[3, 5] = np.nan
+    with pytest.raises(pilot.PilotError) as e:
+        pilot.pilot_search(g, Qs, 10, 64)
+    assert e.value.status == pilot.PILOT_EINVAL
+    ids = np.empty((8, 10), np.int32)
+    dists = np.empty((8, 10), np.float32)
+    with pytest.raises(pilot.PilotError):
+        pilot.pilot_search(g, Qs, 10, 64, ids, dists)
+    ref = oracle.search(oracle_index(idx), np.delete(Qs, 3, 0), 10, 64)
+    assert np.array_equal(np.delete(ids, 3, 0), ref["ids"])
+    assert np.all(ids[3] == -1) and np.all(np.isinf(dists[3]))
+
+
+def test_argument_validation(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    for k, ef in ((0, 10), (11, 10), (10, 513)):
+        with pytest.raises(pilot.PilotError) as e:
+            pilot.pilot_search(g, Q[:2], k, ef)
+        assert e.value.status == pilot.PILOT_EINVAL
+
+
+@pytest.mark.parametrize("name", ["alg1_path_line.json", "alg1_local_minimum.json"])
+def test_golden_traces_on_gpu(pilot, torch_cuda, name):
+    gdata = json.load(open(os.path.join(GOLDEN, name)))
+    X = np.asarray(gdata["points"], np.float32)
+    n, d = X.shape
+    G = np.asarray(gdata["graph"], np.int32)
+    g = pilot.pilot_index_load(G, np.ones(n, np.uint8), G, np.eye(d), X, X, np.asarray([gdata["entry"]], np.int32))
+    for case in gdata["cases"]:
+        ids, dists, cnt = gpu_search(pilot, torch_cuda, g, np.asarray([gdata["query"]], np.float32), case["k"],
+                                     case["ef"], stage1=0, stage2_expansions=0, use_fes=0)
+        assert ids[0].tolist() == case["ids"]
+        np.testing.assert_array_equal(dists[0], np.asarray(case["dists"], np.float32))
+        assert cnt[0, 4] == case["expansions"] and cnt[0, 5] == case["distances"]
+
+
+def test_golden_staged_on_gpu(pilot, torch_cuda):
+    gd = json.load(open(os.path.join(GOLDEN, "staged_2d.json")))
+    X = np.asarray(gd["points"], np.float32)
+    mask = np.asarray(gd["mask"], np.uint8)
+    basis = np.asarray(gd["basis"], np.float64)
+    red = (X[mask == 1].astype(np.float64) @ basis).astype(np.float32)
+    g = pilot.pilot_index_load(np.asarray(gd["graph"], np.int32), mask, np.asarray(gd["subgraph"], np.int32), basis,
+                               red, X, np.asarray(gd["entries"], np.int32))
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, np.asarray([gd["query"]], np.float32), gd["k"], gd["ef"])
+    assert ids[0].tolist() == gd["ids"]
+    np.testing.assert_array_equal(dists[0], np.asarray(gd["dists"], np.float32))
+    assert cnt[0].tolist() == gd["counters"]
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_low_precision_reduced_rows(c1, pilot, torch_cuda, dtype):
+    """BF16 / FP8-E4M3 reduced rows: both sides decode the same codes exactly
+    and accumulate exactly, so results stay identical."""
+    w, idx, Q, red32, _ = c1
+    lp = idx.with_reduced(dtype, red32)
+    g = pilot.load_index_data(lp)
+    ref = oracle.search(oracle_index(lp), Q[:100], 10, 64)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q[:100], 10, 64)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_inner_product_metric(pilot, torch_cuda, dtype):
+    w = synth.WORKLOADS["c3_powerlaw_2m_d768"]
+    idx, Q, red32, _ = index_build.build_workload(w, n=6000, nq=40, reduced_dtype=dtype)
+    g = pilot.load_index_data(idx)
+    ref = oracle.search(oracle_index(idx), Q, 10, 64)
+    # a visited table large enough never to overflow: counters must match too
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 64, hash_log2=13)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+    # the automatic (smaller) table may overflow: same results, more distances
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 64)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.all(cnt[:, [1, 3, 5]] >= ref["counters"][:, [1, 3, 5]])
+
+
+def test_load_from_files(c1, pilot, torch_cuda, tmp_path):
+    w, idx, Q, _, g = c1
+    index_build.save_index(idx, str(tmp_path))
+    g2 = pilot.pilot_index_load_files(str(tmp_path))
+    a = gpu_search(pilot, torch_cuda, g, Q[:20], 10, 64)
+    b = gpu_search(pilot, torch_cuda, g2, Q[:20], 10, 64)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_short_results_are_padded(pilot, torch_cuda):
+    """Fewer than k reachable nodes: -1 ids and +inf distances."""
+    X = np.arange(5, dtype=np.float32)[:, None] * np.ones((1, 4), np.float32)
+    G = np.full((5, 2), -1, np.int32)
+    G[0, 0], G[1, 0] = 1, 2   # 0 -> 1 -> 2; 3 and 4 unreachable
+    g = pilot.pilot_index_load(G, np.ones(5, np.uint8), G, np.eye(4), X, X, np.asarray([0], np.int32))
+    ids, dists, _ = gpu_search(pilot, torch_cuda, g, np.zeros((1, 4), np.float32), 5, 8)
+    assert ids[0].tolist() == [0, 1, 2, -1, -1]
+    assert np.all(np.isinf(dists[0, 3:]))
