@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the staged PilotANN search on B300.
+
+One step = one ``pilot_search`` of a whole query batch (every kernel of the
+path: projection, FES scoring, fused staged search).  Default workload: the
+plain FP32 form, 1,000,000 x 96 unit vectors with a power-law spectrum
+(variance ~ i^-0.8) and a seeded rotation, 10,000 queries, R=32, 30% subgraph,
+d'=32, k=10, L2.  The ef used is the smallest of the sweep {32, 64, 128, 256}
+whose recall@10 against exact FP64 ground truth reaches 0.95; when none does,
+the sweep continues with 384 and 512.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.  Under torchrun each rank holds a
+full replica of the index and searches its own batch (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
+EXTRA_EFS = (384, 512)
+
+
+# ----------------------------------------------------------- distributed --
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda" and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate_throughput(units_per_rank: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
+# ----------------------------------------------------------------- inputs --
+
+def _cache_dir(name: str, n: int | None, nq: int | None) -> str:
+    base = os.environ.get("PILOT_BENCH_CACHE", os.path.join(tempfile.gettempdir(), "pilot_bench_cache"))
+    return os.path.join(base, f"{name}_n{n or 'full'}_q{nq or 'full'}")
+
+
+def load_workload(name: str, n: int | None = None, nq: int | None = None, verbose: bool = True):
+    """(workload, index data, queries, exact top-k ids), cached on disk."""
+    import torch
+    from paper_2503_21206_b300 import index_build, synth
+    w = synth.WORKLOADS[name]
+    cdir = _cache_dir(name, n, nq)
+    if os.path.exists(os.path.join(cdir, "done")):
+        idx = index_build.load_index(cdir)
+        return w, idx, np.load(os.path.join(cdir, "queries.npy")), np.load(os.path.join(cdir, "gt.npy"))
+    dev = "cuda" if torch.cuda.is_available() else None
+    t0 = time.time()
+    idx, Q, _, _ = index_build.build_workload(w, device=dev, n=n, nq=nq)
+    t1 = time.time()
+    gt, _ = index_build.exact_topk(idx.full, Q, w.k, metric=w.metric, device=dev)
+    if verbose:
+        print(f"[bench] built {name}: index {t1 - t0:.1f}s, ground truth {time.time() - t1:.1f}s", file=sys.stderr)
+    os.makedirs(cdir, exist_ok=True)
+    index_build.save_index(idx, cdir)
+    np.save(os.path.join(cdir, "queries.npy"), Q)
+    np.save(os.path.join(cdir, "gt.npy"), gt)
+    open(os.path.join(cdir, "done"), "w").write("ok\n")
+    return w, idx, Q, gt
+
+
+def recall_at_k(found, truth, k):
+    hits = 0
+    for f, t in zip(found[:, :k], truth[:, :k]):
+        hits += len(set(f.tolist()) & set(t.tolist()))
+    return hits / (k * len(found))
+
+
+# -------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu, self.proc, self.path = gpu_index, None, None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(float(r[1]) for r in rows),
+                "sm_max_mhz": max(float(r[2]) for r in rows), "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def algorithmic_bytes(counters: np.ndarray, k: int, idx, T: int = 8) -> float:
+    """Bytes the method must move for one batch, from per-query counters:
+    stage (1): exp1 * 4 R_sub + dist1 * (d' b + s); re-rank: n_rerank * 4 d;
+    stage (2): exp2 * 4 R_sub + dist2 * 4 d; stage (3): exp3 * 4 R + dist3 * 4 d;
+    FES check T (d' b + s); the query (4 d), its projection (4 d') and the output (8 k).
+    b = bytes per reduced element, s = 4 for the FP8 per-row scale."""
+    b = {"f32": 4, "bf16": 2, "fp8": 1}[idx.reduced_dtype]
+    s = 4 if idx.reduced_dtype == "fp8" else 0
+    d, dp, R, Rs = idx.d, idx.dp, idx.graph.shape[1], idx.subgraph.shape[1]
+    c = counters.astype(np.float64)
+    per_q = (c[:, 0] * 4 * Rs + c[:, 1] * (dp * b + s) + c[:, 6] * 4 * d + c[:, 2] * 4 * Rs + c[:, 3] * 4 * d +
+             c[:, 4] * 4 * R + c[:, 5] * 4 * d + T * (dp * b + s) + 4 * d + 4 * dp + 8 * k)
+    return float(per_q.sum())
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("search.cu", "device_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2503_21206_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, ef: int, nq: int):
+    """DRAM bytes per launch of the search kernel from the committed ncu summary
+    (profiles/search_kernel_traffic.json), scaled to nq queries; None when it
+    was taken on another kernel source, workload or ef."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_source_hash() or d.get("workload") != workload or d.get("ef") != ef:
+        return None
+    return float(d["dram_bytes_per_query"]) * nq
+
+
+def oracle_index(idx):
+    import oracle
+    return oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced,
+                              {"f32": 0, "bf16": 1, "fp8": 2}[idx.reduced_dtype], idx.reduced_scales, idx.full,
+                              idx.entry_ids, idx.metric)
+
+
+def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q: int = 4000):
+    """The oracle as it stands, on all host cores, over a bounded query sample.
+    Returns (qps, queries, seconds, threads)."""
+    import oracle
+    oi = oracle_index(idx)
+    threads = os.cpu_count() or 1
+    n = min(min_q, len(Q))
+    t0 = time.perf_counter()
+    oracle.search(oi, Q[:n], k, ef, nthreads=threads)
+    dt = time.perf_counter() - t0
+    if dt < budget_s / 4 and n < len(Q):
+        n = int(min(max_q, len(Q), max(n, n * budget_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.search(oi, Q[:n], k, ef, nthreads=threads)
+        dt = time.perf_counter() - t0
+    return n / dt, n, dt, threads
+
+
+# ------------------------------------------------------------------ arms --
+
+def run_reference(args):
+    """The oracle as the reference arm: same workload, metric and ef rule."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq)
+    threads = os.cpu_count() or 1
+    oi = oracle_index(idx)
+    ef = args.ef
+    if not ef:   # the GPU arm's rule, judged on a 256-query sample
+        ns = min(256, len(Q))
+        for cand in list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]:
+            ef = cand
+            r = oracle.search(oi, Q[:ns], w.k, cand, nthreads=threads)
+            if recall_at_k(r["ids"], gt[:ns], w.k) >= 0.95:
+                break
+    qps0, _, _, _ = oracle_sample(idx, Q, w.k, ef, budget_s=2.0, min_q=32, max_q=256)
+    per_step = int(max(16, min(len(Q), qps0 * 8.0)))
+    for _ in range(args.warmup):
+        oracle.search(oi, Q[:16], w.k, ef, nthreads=threads)
+    times, hits = [], []
+    for s in range(args.steps):
+        lo = (s * per_step) % max(1, len(Q) - per_step + 1)
+        t0 = time.perf_counter()
+        r = oracle.search(oi, Q[lo:lo + per_step], w.k, ef, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+        hits.append(recall_at_k(r["ids"], gt[lo:lo + per_step], w.k))
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": "QPS@recall10=0.95", "value": value, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 accumulate, f32-rounded distances", "data": "synthetic",
+            "config": {"workload": args.workload, "n": idx.n, "d": idx.d, "nq": len(Q), "k": w.k, "ef": ef,
+                       "recall@10": round(float(np.mean(hits)), 5), "l2": "n/a (host cores)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} of {len(Q)} queries per step, ef={ef}, {threads} threads"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_pilot(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    from paper_2503_21206_b300 import pilot
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq, verbose=(rank == 0))
+    nq, k = len(Q), w.k
+    g = pilot.load_index_data(idx)
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    cnt = torch.empty((nq, 8), dtype=torch.int32, device=device)
+    kms = np.zeros(3, np.float32)
+    opts = pilot.pilot_search_options_default()
+    if args.hash_log2:
+        opts.hash_log2 = args.hash_log2
+    if args.warps_per_block:
+        opts.warps_per_block = args.warps_per_block
+
+    def search(q, ef, o_ids, o_d, counters=None, timing=kms):
+        return pilot.pilot_search_ex(g, q, k, ef, o_ids, o_d, stream, options=opts, counters=counters,
+                                     kernel_ms=timing)
+
+    # operating point: the smallest swept ef reaching recall@10 >= 0.95
+    efs = [args.ef] if args.ef else list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
+    sweep, ef = [], None
+    for cand in efs:
+        search(qd, cand, ids, dists, cnt)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt, k)
+        sweep.append({"ef": cand, "recall@10": round(rec, 5), "search_ms": round(float(kms[2]), 4)})
+        ef = cand
+        if rec >= 0.95:
+            break
+    search(qd, ef, ids, dists, cnt)
+    torch.cuda.synchronize()
+    counters = cnt.cpu().numpy()
+    recall = recall_at_k(ids.cpu().numpy(), gt, k)
+    alg_bytes = algorithmic_bytes(counters, k, idx)
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        search(qd, ef, ids, dists)
+
+    # ---- device-timed steps: inputs resident in HBM, L2 flushed between steps
+    step_ms, search_ms = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(device)
+    torch.cuda.synchronize()
+    with ClockSampler(device.index or 0) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            ev0.record(stream)
+            search(qd, ef, ids, dists)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            search_ms.append(float(kms[2]))
+        torch.cuda.synchronize()
+        barrier(device)
+        t_wall = time.perf_counter() - t_wall
+    clocks = clk.summary()
+    max_s = reduce_max(sum(step_ms) / 1000.0, device)
+    value = aggregate_throughput(nq * args.steps, ws, max_s)
+
+    # ---- end to end through the C ABI with pinned HOST buffers (copies timed)
+    qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    dists_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    e2e_s = []
+    for _ in range(max(1, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pilot.pilot_search(g, qh, k, ef, ids_h, dists_h, stream)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_value = aggregate_throughput(nq * len(e2e_s), ws, reduce_max(sum(e2e_s), device))
+    e2e_recall = recall_at_k(ids_h.numpy(), gt, k)
+
+    peak, peak_kind = measured_peaks()
+    mean_search_ms = statistics.mean(search_ms)
+    achieved = alg_bytes / (mean_search_ms / 1000.0) / 1e9
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        qps, ns, secs, threads = oracle_sample(idx, Q, k, ef)
+        cpu = {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {ns} of {nq} queries, ef={ef}, {secs:.1f}s on {threads} host threads"}
+    c = counters.astype(np.float64)
+    line = {
+        "metric": "QPS@recall10=0.95", "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * max_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": idx.n, "d": idx.d, "dp": idx.dp, "nq": nq, "k": k, "ef": ef,
+                   "recall@10": round(recall, 5), "R": int(idx.graph.shape[1]), "sample_ratio": w.sample_ratio,
+                   "n_entry": int(len(idx.entry_ids)), "reduced_dtype": idx.reduced_dtype,
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "sweep": sweep,
+                   "parallelism": f"replicas x{ws}",
+                   "mean_counters": {name: round(float(c[:, i].mean()), 2) for i, name in
+                                     enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}},
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(nq * idx.d * 4),
+                "d2h_bytes_per_step": int(nq * k * 8), "recall@10": round(e2e_recall, 5)},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"kernel": "search_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(args.workload, ef, nq),
+                     "peak_source": f"{peak_kind} hbm_gbs (copy)", "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_kernel_ms": mean_search_ms},
+        "kernel_ms": {"project": float(kms[0]), "fes_scores": float(kms[1]), "search": mean_search_ms},
+        "clocks": clocks, "wall_s_timed": round(t_wall, 4),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="PilotANN staged search benchmark")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pilot", "reference"], default="pilot")
+    ap.add_argument("--workload", default="c2_aniso_1m_d96")
+    ap.add_argument("--ef", type=int, default=0, help="a fixed ef instead of the recall-0.95 sweep")
+    ap.add_argument("--n", type=int, default=None, help="smaller base set (profiling cases)")
+    ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling cases)")
+    ap.add_argument("--hash-log2", type=int, default=0)
+    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return run_reference(args) if args.impl == "reference" else run_pilot(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

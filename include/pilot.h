@@ -127,6 +127,9 @@ typedef struct {
     int32_t* counters;          /* optional nq x 8 int32 (host or device): per query the
                                    expansions and distances of stages (1), (2), (3), the
                                    number of re-ranked candidates and the entry id */
+    float* kernel_ms;           /* optional HOST array of 3 floats: device time in ms of the
+                                   projection, FES scoring and search kernels of this call,
+                                   from CUDA events recorded on the call's stream */
 } pilot_search_options;
 
 void pilot_search_options_default(pilot_search_options* opt);

@@ -38,7 +38,7 @@ pilot_status fail(pilot_status s, const char* fmt, ...) {
     do {                                                                                            \
         cudaError_t e__ = (expr);                                                                   \
         if (e__ != cudaSuccess)                                                                     \
-            return fail(e__ == cudaErrorMemoryAllocation ? PILOT_ENOMEM : PILOT_ECUDA, "%s: %s (%s:%d)", \
+            return cudaGetLastError(), fail(e__ == cudaErrorMemoryAllocation ? PILOT_ENOMEM : PILOT_ECUDA, "%s: %s (%s:%d)", \
                         #expr, cudaGetErrorString(e__), __FILE__, __LINE__);                        \
     } while (0)
 
@@ -70,8 +70,11 @@ struct pilot_index {
     size_t ws_bytes = 0;
     int32_t* status_host = nullptr;   // pinned
     size_t device_bytes = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // per-kernel timing (on request)
 
     ~pilot_index() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
         if (ws) cudaFree(ws);
         if (status_host) cudaFreeHost(status_host);
@@ -476,9 +479,24 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (!q_dev)
         CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(io.queries), queries, size_t(nq) * X.d * 4,
                                  cudaMemcpyHostToDevice, st));
+    const bool timed = opt.kernel_ms != nullptr;
+    if (timed && !ix->ev[0])
+        for (cudaEvent_t& e : ix->ev) CUDA_TRY(cudaEventCreate(&e));
+    if (timed) CUDA_TRY(cudaEventRecord(ix->ev[0], st));
     CUDA_TRY(launch_project(X, io, st));
+    if (timed) CUDA_TRY(cudaEventRecord(ix->ev[1], st));
     if (cfg.use_fes) CUDA_TRY(launch_fes_scores(X, cfg, io, st));
-    CUDA_TRY(launch_search(X, cfg, io, st, ix->num_sms));
+    if (timed) CUDA_TRY(cudaEventRecord(ix->ev[2], st));
+    {
+        cudaError_t e = launch_search(X, cfg, io, st, ix->num_sms);
+        if (e == cudaErrorInvalidConfiguration) {
+            cudaGetLastError();
+            return fail(PILOT_EINVAL, "per-block shared memory (%zu B per warp x %d warps) exceeds the device limit; "
+                        "lower hash_log2, ef or warps_per_block", search_smem_per_warp(X, cfg), cfg.warps_per_block);
+        }
+        CUDA_TRY(e);
+    }
+    if (timed) CUDA_TRY(cudaEventRecord(ix->ev[3], st));
     if (!ids_dev) CUDA_TRY(cudaMemcpyAsync(out_ids, io.out_ids, size_t(nq) * k * 4, cudaMemcpyDeviceToHost, st));
     if (!dists_dev)
         CUDA_TRY(cudaMemcpyAsync(out_dists, io.out_dists, size_t(nq) * k * 4, cudaMemcpyDeviceToHost, st));
@@ -486,6 +504,8 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
         CUDA_TRY(cudaMemcpyAsync(opt.counters, io.counters, size_t(nq) * 8 * 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(ix->status_host, io.status, 8 * 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (timed)
+        for (int i = 0; i < 3; ++i) CUDA_TRY(cudaEventElapsedTime(&opt.kernel_ms[i], ix->ev[i], ix->ev[i + 1]));
     const int32_t* S = ix->status_host;
     if (S[4]) return fail(PILOT_ECUDA, "%d queries hit the expansion cap", S[4]);
     if (S[0]) return fail(PILOT_EINVAL, "%d queries hold NaN or infinity (their results are -1 / +inf)", S[0]);

@@ -494,6 +494,10 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO
                      int num_sms) {
     const Layout L = make_layout(ix, cfg);
     const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, METRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;

@@ -44,7 +44,7 @@ class pilot_index_desc(ctypes.Structure):
 class pilot_search_options(ctypes.Structure):
     _fields_ = [("stage1", ctypes.c_int32), ("stage2_expansions", ctypes.c_int32), ("stage3", ctypes.c_int32),
                 ("use_fes", ctypes.c_int32), ("hash_log2", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("counters", ctypes.c_void_p)]
+                ("counters", ctypes.c_void_p), ("kernel_ms", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -156,7 +156,7 @@ def pilot_index_load_files(path: str) -> PilotIndex:
 
 
 def pilot_search(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_dists=None, stream=None, *,
-                 options: pilot_search_options | None = None, counters=None):
+                 options: pilot_search_options | None = None, counters=None, kernel_ms=None):
     """Top-k search.  ``queries`` is an nq x d float32 numpy array or torch
     tensor (host or CUDA); outputs default to host numpy arrays.  ``stream``
     is a torch.cuda.Stream (or raw handle).  Returns (ids, dists)."""
@@ -168,22 +168,24 @@ def pilot_search(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_
     s = None
     if stream is not None:
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    if options is None and counters is None:
+    if options is None and counters is None and kernel_ms is None:
         _check(_lib.pilot_search(index.handle, _addr(queries), nq, k, ef, _addr(out_ids), _addr(out_dists), s))
     else:
         o = options if options is not None else pilot_search_options_default()
         o.counters = _addr(counters)
+        o.kernel_ms = _addr(kernel_ms)
         _check(_lib.pilot_search_ex(index.handle, _addr(queries), nq, k, ef, _addr(out_ids), _addr(out_dists), s,
                                     ctypes.byref(o)))
     return out_ids, out_dists
 
 
 def pilot_search_ex(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_dists=None, stream=None,
-                    options: pilot_search_options | None = None, counters=None):
-    """pilot_search with explicit options (``pilot_search_options``)."""
+                    options: pilot_search_options | None = None, counters=None, kernel_ms=None):
+    """pilot_search with explicit options (``pilot_search_options``).
+    ``kernel_ms`` (a float32 numpy array of 3) receives per-kernel device times."""
     return pilot_search(index, queries, k, ef, out_ids, out_dists, stream,
                         options=options if options is not None else pilot_search_options_default(),
-                        counters=counters)
+                        counters=counters, kernel_ms=kernel_ms)
 
 
 def pilot_index_info(index: PilotIndex) -> dict:
