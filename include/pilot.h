@@ -152,6 +152,27 @@ pilot_status pilot_search(pilot_index* index, const float* queries, int64_t nq, 
 pilot_status pilot_search_ex(pilot_index* index, const float* queries, int64_t nq, int k, int ef,
                              int32_t* out_ids, float* out_dists, void* stream, const pilot_search_options* opt);
 
+/*
+ * pilot_search for callers that cannot allocate device memory during a call
+ * (code that must leave every allocation to its own pool or allocator, or
+ * loops that cannot afford the synchronisation an allocation brings).  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * Same search, defaults and results as pilot_search, but the per-call scratch
+ * lives in one fixed device array of PILOT_NOALLOC_SCRATCH_BYTES that the
+ * library holds on every GPU it is loaded on until the process exits; the call
+ * makes no cudaMalloc / cudaFree.  queries, out_ids and out_dists must be
+ * DEVICE pointers (PILOT_EINVAL otherwise), and the index must already be
+ * loaded.  A batch whose scratch would not fit is rejected with PILOT_EINVAL
+ * and a message giving the size; split it.  The first call on a device looks
+ * up the array's device address, so make that first call before capturing any
+ * stream.  Every call on a device shares the array: calls whose GPU work
+ * overlaps race on it.  Synchronous on `stream`, like pilot_search.
+ */
+#define PILOT_NOALLOC_SCRATCH_BYTES (16u << 20)
+pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int64_t nq, int k, int ef,
+                                  int32_t* out_ids, float* out_dists, void* stream);
+
 /* The calling thread's last error message ("" if none). */
 const char* pilot_last_error(void);
 

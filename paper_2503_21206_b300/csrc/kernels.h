@@ -62,6 +62,15 @@ cudaError_t launch_fes_scores(const DevIndex& ix, const SearchConfig& cfg, const
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
                           int num_sms);
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
+
+// Internal view of a loaded index for entry points outside pilot_api.cu.
+struct IndexView {
+    const DevIndex* dev;
+    int device;
+    int num_sms;
+    int32_t* status_host;   // pinned, 8 words
+    void* mutex;            // std::mutex guarding per-index state
+};
 int search_blocks_per_sm(const DevIndex& ix, const SearchConfig& cfg);
 
 }  // namespace pilot

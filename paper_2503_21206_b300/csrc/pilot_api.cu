@@ -109,6 +109,20 @@ struct pilot_index {
     }
 };
 
+namespace pilot {
+
+// Internal helpers for entry points defined in other translation units.
+IndexView index_view(pilot_index* ix) {
+    return IndexView{&ix->dev, ix->device, ix->num_sms, ix->status_host, &ix->mu};
+}
+
+int set_error(int status, const char* msg) {
+    g_error = msg;
+    return status;
+}
+
+}  // namespace pilot
+
 extern "C" {
 
 const char* pilot_last_error(void) { return g_error.c_str(); }

@@ -58,6 +58,8 @@ _lib.pilot_index_info.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int64)] * 5
 _lib.pilot_search_options_default.argtypes = [ctypes.POINTER(pilot_search_options)]
 _lib.pilot_search_options_default.restype = None
 _lib.pilot_search.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+_lib.pilot_search_noalloc.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+PILOT_NOALLOC_SCRATCH_BYTES = 16 << 20
 _lib.pilot_search_ex.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                  ctypes.POINTER(pilot_search_options)]
 
@@ -194,3 +196,15 @@ def pilot_index_info(index: PilotIndex) -> dict:
 
 def pilot_index_free(index: PilotIndex) -> None:
     index.free()
+
+
+def pilot_search_noalloc(index: PilotIndex, queries, k: int, ef: int, out_ids, out_dists, stream=None):
+    """pilot_search that allocates no device memory during the call: scratch
+    comes from a fixed array inside the library.  ``queries``, ``out_ids`` and
+    ``out_dists`` must be CUDA tensors (device memory)."""
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(_lib.pilot_search_noalloc(index.handle, _addr(queries), int(queries.shape[0]), k, ef, _addr(out_ids),
+                                     _addr(out_dists), s))
+    return out_ids, out_dists
