@@ -62,6 +62,9 @@ cudaError_t launch_fes_scores(const DevIndex& ix, const SearchConfig& cfg, const
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
                           int num_sms);
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
+// The defaults of every search entry point (stages as in the paper, T = 8 FES
+// survivors, automatic visited-table and staging sizes).
+SearchConfig default_search_config(const DevIndex& ix, int k, int ef);
 
 // Internal view of a loaded index for entry points outside pilot_api.cu.
 struct IndexView {

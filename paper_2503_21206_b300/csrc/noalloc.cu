@@ -98,21 +98,7 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     const DevIndex& X = *v.dev;
 
     // the same defaults as pilot_search
-    SearchConfig cfg{};
-    cfg.k = k;
-    cfg.ef = ef;
-    cfg.stage1 = 1;
-    cfg.stage2_expansions = 2;
-    cfg.stage3 = 1;
-    cfg.use_fes = 1;
-    cfg.fes_T = 8;
-    cfg.warps_per_block = 4;
-    int hl = 10;
-    while ((1 << hl) < 8 * ef && hl < 13) ++hl;
-    cfg.hash_log2 = hl;
-    int stage = std::max(4 * X.full_row_bytes, 4 * X.red_row_bytes);
-    stage = std::max(stage, std::min(32 * X.full_row_bytes, 16384));
-    cfg.stage_bytes = std::max(stage, 32 * X.red_row_bytes);
+    const SearchConfig cfg = default_search_config(X, k, ef);
 
     // scratch layout inside the static array
     size_t off = 0;

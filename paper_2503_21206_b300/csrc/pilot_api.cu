@@ -426,26 +426,14 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const DevIndex& X = ix->dev;
 
-    SearchConfig cfg{};
-    cfg.k = k;
-    cfg.ef = ef;
+    SearchConfig cfg = default_search_config(X, k, ef);
     cfg.stage1 = opt.stage1 != 0;
     cfg.stage2_expansions = opt.stage2_expansions;
     cfg.stage3 = opt.stage3 != 0;
     cfg.use_fes = opt.use_fes != 0;
-    cfg.fes_T = 8;
-    cfg.warps_per_block = opt.warps_per_block > 0 ? std::min(opt.warps_per_block, 8) : 4;
-    int hl = opt.hash_log2;
-    if (hl <= 0) {
-        hl = 10;
-        while ((1 << hl) < 8 * ef && hl < 13) ++hl;
-    }
-    if (hl < 5 || hl > 16) return fail(PILOT_EINVAL, "hash_log2 = %d out of [5, 16]", hl);
-    cfg.hash_log2 = hl;
-    int stage = std::max(4 * X.full_row_bytes, 4 * X.red_row_bytes);
-    stage = std::max(stage, std::min(32 * X.full_row_bytes, 16384));
-    stage = std::max(stage, 32 * X.red_row_bytes);
-    cfg.stage_bytes = stage;
+    if (opt.warps_per_block > 0) cfg.warps_per_block = std::min(opt.warps_per_block, 8);
+    if (opt.hash_log2 > 0) cfg.hash_log2 = opt.hash_log2;
+    if (cfg.hash_log2 < 5 || cfg.hash_log2 > 16) return fail(PILOT_EINVAL, "hash_log2 = %d out of [5, 16]", cfg.hash_log2);
 
     const bool q_dev = is_device_ptr(queries);
     const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);

@@ -32,7 +32,7 @@ constexpr int kMaxExpansionsPerStage = 1 << 22;
 
 struct Layout {
     int pool_cap;      // power of two >= ef
-    int off_pool0, off_pool1, off_hash, off_cand, off_dist, off_bkeys, off_q, off_qp, off_stage;
+    int off_pool0, off_hash, off_cand, off_dist, off_bkeys, off_q, off_qp, off_stage;
     int per_warp;
 };
 
@@ -49,7 +49,6 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
     L.pool_cap = pow2_ceil(cfg.ef < 32 ? 32 : cfg.ef);
     int o = 0;
     L.off_pool0 = o; o += L.pool_cap * 8;
-    L.off_pool1 = o; o += L.pool_cap * 8;
     L.off_hash = o; o += (1 << cfg.hash_log2) * 4;
     L.off_cand = o; o += kCand * 4;
     L.off_dist = o; o += kCand * 4;
@@ -65,7 +64,6 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
 
 struct Warp {
     uint64_t* pool;
-    uint64_t* other;
     uint32_t* hash;
     int32_t* cand;
     float* dist;
@@ -74,6 +72,7 @@ struct Warp {
     float* qp;
     uint8_t* stage;
     int S;          // candidates in C
+    int lb;         // every candidate before position lb is checked
     int log2h;
     int overflow;
     int lane;
@@ -91,6 +90,7 @@ __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ 
     const int F8 = row_bytes >> 7;   // 16-byte chunks per lane per row
     int P = stage_bytes / row_bytes;
     P = P >= kCand ? kCand : (P & ~3);
+    const int jrows = (m + 3) >> 2;   // row slots any lane needs (warp-uniform)
     DF acc[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j] = DF{0.0f, 0.0f};
@@ -108,10 +108,12 @@ __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int r = g + 4 * j;
-            if (r >= r0 && r < r0 + P && r < m) {
+            // every lane works on row slot j when any lane needs it (rows past m
+            // hold stale data whose result is discarded), so the warp stays converged
+            if (j < jrows && 4 * j >= r0 && 4 * j < r0 + P) {
                 const uint8_t* srow = w.stage + (r - r0) * row_bytes;
                 float sc = 1.0f;
-                if (DT == 2) sc = __ldg(scales + w.cand[r]);
+                if (DT == 2) sc = r < m ? __ldg(scales + w.cand[r]) : 1.0f;
                 for (int t = 0; t < F8; ++t) {
                     const int c = mm + 8 * t;
                     uint4 v = *reinterpret_cast<const uint4*>(srow + c * 16);
@@ -193,50 +195,51 @@ __device__ __forceinline__ uint64_t warp_min(uint64_t v) {
     return v;
 }
 
-// Merge nb sorted new keys (one per lane, kKeyEmpty beyond nb) into C.
-// Keys already in C (same distance and id) are dropped.  C keeps its ef best.
+// Merge nb sorted new keys (lanes 0..nb-1, kKeyEmpty beyond) into C in place.
+// A new key equal to one already in C (same distance and id) is dropped.  Each
+// kept key lands at (its rank among the new keys) + (its lower bound in C);
+// output positions are filled from the last 32-slot chunk down to the first
+// changed one, every lane reading its source before any lane writes, so an
+// element is always read before it is overwritten.  C keeps its ef best.
 __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef) {
     const int lane = w.lane;
-    const uint64_t* A = w.pool;
+    uint64_t* A = w.pool;
     const int S = w.S;
-    int rankA = 0;
-    bool dup = false;
-    if (lane < nb) {
-        int lo = 0, hi = S;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if ((A[mid] & ~1ull) < key) lo = mid + 1;
-            else hi = mid;
-        }
-        rankA = lo;
-        dup = lo < S && (A[lo] & ~1ull) == key;
-    }
-    const unsigned keep = __ballot_sync(kFull, lane < nb && !dup);
+    // lower bound of every new key in C, in lock step (fixed step count)
+    int p = 0;
+    for (int step = S > 0 ? (1 << (31 - __clz(S))) : 0; step > 0; step >>= 1)
+        if (p + step <= S && (A[p + step - 1] & ~1ull) < key) p += step;
+    const bool dup = lane < nb && p < S && (A[p] & ~1ull) == key;
+    const bool mine = lane < nb && !dup;
+    const unsigned keep = __ballot_sync(kFull, mine);
     const int nb2 = __popc(keep);
+    if (nb2 == 0) return;
     const int ci = __popc(keep & lanemask_lt());
-    if (lane < nb && !dup) w.bkeys[ci] = key;
+    const int np = mine ? p + ci : 0x7FFFFFFF;
+    if (mine) w.bkeys[ci] = key;
+    const int Snew = min(S + nb2, ef);
+    const int lo_pos = __reduce_min_sync(kFull, np);
     __syncwarp();
-    uint64_t* out = w.other;
-    for (int x = lane; x < S; x += 32) {
-        const uint64_t a = A[x];
-        const uint64_t am = a & ~1ull;
-        int lo = 0, hi = nb2;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (w.bkeys[mid] < am) lo = mid + 1;
-            else hi = mid;
+    if (lo_pos >= Snew) return;
+    for (int c = (Snew - 1) >> 5; c >= (lo_pos >> 5); --c) {
+        const int base = c << 5;
+        const int pos = base + lane;
+        const unsigned bit = (mine && np >= base && np < base + 32) ? (1u << (np - base)) : 0u;
+        const unsigned mask_c = __reduce_or_sync(kFull, bit);
+        const int before = __popc(__ballot_sync(kFull, mine && np < base));
+        const bool write = pos < Snew && pos >= lo_pos;
+        uint64_t val = 0;
+        if (write) {
+            const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+            const int kle = before + __popc(mask_c & upto);
+            val = ((mask_c >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos - kle];
         }
-        const int np = x + lo;
-        if (np < ef) out[np] = a;
+        __syncwarp();
+        if (write) A[pos] = val;
+        __syncwarp();
     }
-    if (lane < nb && !dup) {
-        const int np = ci + rankA;
-        if (np < ef) out[np] = key;
-    }
-    __syncwarp();
-    w.other = w.pool;
-    w.pool = out;
-    w.S = min(S + nb2, ef);
+    w.S = Snew;
+    if (lo_pos < w.lb) w.lb = lo_pos;
 }
 
 // Ascending bitonic sort of C in place (the re-rank), padded to a power of two.
@@ -279,47 +282,57 @@ struct Searcher {
                               cfg.stage_bytes);
     }
 
+    // Adjacency row of node u in a view (null if it has none).
+    __device__ __forceinline__ const int32_t* adjacency(int view, int32_t u) const {
+        if (view == 1) return ix.sub_adj + int64_t(u) * ix.R_sub;
+        if (view == 2) {
+            const int32_t cu = __ldg(ix.full2sub + u);   // every stage (2) candidate is sampled
+            return cu < 0 ? nullptr : ix.sub_adj + int64_t(cu) * ix.R_sub;
+        }
+        return ix.graph + int64_t(u) * ix.R;
+    }
+
     // One step of Algorithm 1.  view 1: subgraph + reduced rows, compact ids;
     // view 2: subgraph + full rows, original ids; view 3: full graph + full
     // rows.  Returns false when C has no unchecked candidate.
     __device__ bool expand(int view, int& n_exp, int& n_dist) {
         const int lane = w.lane;
-        int idx = -1;
-        for (int b0 = 0; b0 < w.S; b0 += 32) {
+        int idx = -1, idx2 = -1;
+        for (int b0 = w.lb; b0 < w.S; b0 += 32) {
             const int i = b0 + lane;
             const bool unc = i < w.S && !(w.pool[i] & 1ull);
             const unsigned b = __ballot_sync(kFull, unc);
             if (b) {
                 idx = b0 + __ffs(b) - 1;
+                const unsigned b2 = b & (b - 1);
+                if (b2) idx2 = b0 + __ffs(b2) - 1;
                 break;
             }
         }
-        if (idx < 0) return false;
+        if (idx < 0) {
+            w.lb = w.S;
+            return false;
+        }
         const uint64_t key = w.pool[idx];
         __syncwarp();
         if (lane == 0) w.pool[idx] = key | 1ull;
-        __syncwarp();
+        w.lb = idx + 1;
         n_exp += 1;
         const int32_t u = key_id(key);
-        const int32_t* row;
-        int W;
-        if (view == 1) {
-            row = ix.sub_adj + int64_t(u) * ix.R_sub;
-            W = ix.R_sub;
-        } else if (view == 2) {
-            const int32_t cu = __ldg(ix.full2sub + u);
-            row = ix.sub_adj + int64_t(cu < 0 ? 0 : cu) * ix.R_sub;
-            W = cu < 0 ? 0 : ix.R_sub;   // every stage (2) candidate is sampled
-        } else {
-            row = ix.graph + int64_t(u) * ix.R;
-            W = ix.R;
+        const int32_t* row = adjacency(view, u);
+        const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
+        // the next expansion most likely takes the second unchecked candidate:
+        // bring its adjacency row into L2 while this one is processed
+        if (idx2 >= 0 && lane == 0) {
+            const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
+            if (r2) asm volatile("prefetch.global.L2 [%0];" ::"l"(r2));
         }
+        __syncwarp();
         for (int b0 = 0; b0 < W; b0 += 32) {
             const int j = b0 + lane;
             int32_t v = j < W ? __ldg(row + j) : -1;
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
-            bool isnew = false;
-            if (v >= 0) isnew = hash_insert(w.hash, w.log2h, uint32_t(v), w.overflow);
+            const bool isnew = hash_insert_warp(w.hash, w.log2h, uint32_t(v), v >= 0, w.overflow);
             const unsigned nb = __ballot_sync(kFull, isnew);
             const int cnt = __popc(nb);
             if (cnt == 0) continue;
@@ -330,8 +343,12 @@ struct Searcher {
             __syncwarp();
             n_dist += cnt;
             uint64_t k = lane < cnt ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
+            // a full list only admits keys below its worst one
+            if (w.S == cfg.ef && k >= (w.pool[w.S - 1] & ~1ull)) k = kKeyEmpty;
+            const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
+            if (nkeep == 0) continue;
             k = warp_sort32(k, lane);
-            merge_new(w, k, cnt, cfg.ef);
+            merge_new(w, k, nkeep, cfg.ef);
         }
         return true;
     }
@@ -386,8 +403,9 @@ struct Searcher {
         hash_clear(w.hash, w.log2h, lane);
         if (lane == 0) w.pool[0] = best;
         w.S = 1;
+        w.lb = 0;
         __syncwarp();
-        if (lane == 0) hash_insert(w.hash, w.log2h, uint32_t(key_id(best)), w.overflow);
+        hash_insert_warp(w.hash, w.log2h, uint32_t(key_id(best)), lane == 0, w.overflow);
         __syncwarp();
         bool capped = false;
         if (cfg.stage1) {
@@ -411,13 +429,12 @@ struct Searcher {
             __syncwarp();
             full_batch(m);
             __syncwarp();
-            if (lane < m) {
-                w.pool[b0 + lane] = make_key(w.dist[lane], orig);
-                hash_insert(w.hash, w.log2h, uint32_t(orig), w.overflow);
-            }
+            if (lane < m) w.pool[b0 + lane] = make_key(w.dist[lane], orig);
+            hash_insert_warp(w.hash, w.log2h, uint32_t(orig), lane < m, w.overflow);
             __syncwarp();
         }
         sort_pool(w, 0x7FFFFFFF);
+        w.lb = 0;
 
         // ---- stage (2): a fixed number of subgraph expansions, full rows
         for (int it = 0; it < cfg.stage2_expansions; ++it)
@@ -426,6 +443,7 @@ struct Searcher {
         // ---- stage (3): Algorithm 1 on the full graph, all unchecked
         if (cfg.stage3) {
             for (int i = lane; i < w.S; i += 32) w.pool[i] &= ~1ull;
+            w.lb = 0;
             __syncwarp();
             int it = 0;
             while (expand(3, e3, d3))
@@ -459,7 +477,6 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
     uint8_t* base = smem + size_t(warp) * L.per_warp;
     Warp w;
     w.pool = reinterpret_cast<uint64_t*>(base + L.off_pool0);
-    w.other = reinterpret_cast<uint64_t*>(base + L.off_pool1);
     w.hash = reinterpret_cast<uint32_t*>(base + L.off_hash);
     w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
     w.dist = reinterpret_cast<float*>(base + L.off_dist);
@@ -471,6 +488,7 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
     w.overflow = 0;
     w.lane = threadIdx.x & 31;
     w.S = 0;
+    w.lb = 0;
     Searcher<DT, METRIC> s{ix, cfg, w};
     for (;;) {
         int64_t q = 0;
@@ -517,6 +535,26 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO
 }  // namespace
 
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg) { return make_layout(ix, cfg).per_warp; }
+
+SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
+    SearchConfig cfg{};
+    cfg.k = k;
+    cfg.ef = ef;
+    cfg.stage1 = 1;
+    cfg.stage2_expansions = 2;
+    cfg.stage3 = 1;
+    cfg.use_fes = 1;
+    cfg.fes_T = 8;
+    cfg.warps_per_block = 2;
+    int hl = 10;
+    while ((1 << hl) < 8 * ef && hl < 13) ++hl;
+    cfg.hash_log2 = hl;
+    int stage = 4 * (ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes);
+    const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;
+    stage = stage > full32 ? stage : full32;
+    cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
+    return cfg;
+}
 
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
                           int num_sms) {
