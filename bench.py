@@ -283,8 +283,6 @@ def run_pilot(args):
     cnt = torch.empty((nq, 8), dtype=torch.int32, device=device)
     kms = np.zeros(3, np.float32)
     opts = pilot.pilot_search_options_default()
-    if args.hash_log2:
-        opts.hash_log2 = args.hash_log2
     if args.warps_per_block:
         opts.warps_per_block = args.warps_per_block
 
@@ -399,7 +397,6 @@ def main(argv=None):
     ap.add_argument("--ef", type=int, default=0, help="a fixed ef instead of the recall-0.95 sweep")
     ap.add_argument("--n", type=int, default=None, help="smaller base set (profiling cases)")
     ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling cases)")
-    ap.add_argument("--hash-log2", type=int, default=0)
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

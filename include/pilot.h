@@ -92,7 +92,12 @@ typedef struct {
     const int32_t* entry_ids;
 } pilot_index_desc;
 
-/* Copy an index to the current CUDA device.  *out receives the handle. */
+/*
+ * Copy an index to the current CUDA device.  *out receives the handle.  Besides
+ * the arrays, the index holds the searches' visited sets: one byte per node
+ * for each resident search warp (up to 16 per SM, within a quarter of the free
+ * device memory), e.g. about 2.4 GB at n = 1M on a 148-SM GPU.
+ */
 pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
 
 /*
@@ -122,7 +127,6 @@ typedef struct {
     int32_t stage2_expansions;  /* stage (2) subgraph expansions (default 2, Sec. 4.1 (2)) */
     int32_t stage3;             /* 1: run stage (3) (default 1) */
     int32_t use_fes;            /* 1: FES entry (default); 0: entry_ids[0] */
-    int32_t hash_log2;          /* visited table 2^hash_log2 slots per query; 0 = automatic */
     int32_t warps_per_block;    /* 0 = automatic */
     int32_t* counters;          /* optional nq x 8 int32 (host or device): per query the
                                    expansions and distances of stages (1), (2), (3), the

@@ -16,7 +16,6 @@ namespace pilot {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint64_t kKeyEmpty = ~0ull;
-constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------ FP32 pairs --
 
@@ -162,53 +161,6 @@ __device__ __forceinline__ uint64_t warp_sort32(uint64_t v, int lane) {
         }
     }
     return v;
-}
-
-// ---------------------------------------------------------- visited hash --
-// Exact open-addressing set of node ids in shared memory (linear probing,
-// multiplicative hashing).  When 16 probed slots are all taken by other ids
-// the insert fails and the id is treated as unvisited; the candidate merge
-// then drops it if it is already in the list.  That keeps results exactly
-// those of an unbounded visited set: a re-computed node that is not in the
-// list was cut earlier, when the list was full and its worst key was lower,
-// and the worst key of a full list never rises, so it is cut again.
-
-__device__ __forceinline__ void hash_clear(uint32_t* tab, int log2h, int lane) {
-    uint4* t4 = reinterpret_cast<uint4*>(tab);
-    const int n4 = (1 << log2h) >> 2;
-    for (int i = lane; i < n4; i += 32) t4[i] = make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty);
-}
-
-// Warp-wide insert: each lane offers one key (valid = false for none).
-// Returns true where the key was absent (now inserted, or not recordable);
-// false where it was present.  The probe loop runs in lock step and ends when
-// every lane is done, so the warp never diverges across probe rounds.
-__device__ __forceinline__ bool hash_insert_warp(uint32_t* tab, int log2h, uint32_t key, bool valid,
-                                                 int& overflow) {
-    const uint32_t mask = (1u << log2h) - 1u;
-    const uint32_t h = (key * 2654435761u) >> (32 - log2h);
-    volatile uint32_t* vt = tab;
-    bool done = !valid, fresh = false;
-#pragma unroll 1
-    for (int p = 0; p < 16; ++p) {
-        if (!done) {
-            const uint32_t s = (h + uint32_t(p)) & mask;
-            const uint32_t cur = vt[s];
-            if (cur == key) {
-                done = true;
-            } else if (cur == kSlotEmpty) {
-                const uint32_t old = atomicCAS(&tab[s], kSlotEmpty, key);
-                if (old == kSlotEmpty) done = fresh = true;
-                else if (old == key) done = true;
-            }
-        }
-        if (__all_sync(kFull, done)) break;
-    }
-    if (!done) {
-        overflow += 1;
-        fresh = true;
-    }
-    return valid && fresh;
 }
 
 // ------------------------------------------------------------- cp.async --

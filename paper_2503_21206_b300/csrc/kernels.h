@@ -30,12 +30,19 @@ struct DevIndex {
     const float* entry_f32;    // n_entry x qp_pad, exact decoded reduced rows of the entries
     const float* entry_norm2;  // n_entry, ||e||^2 (FP32 of the FP64 value)
     float entry_max_norm;      // max ||e||
+    // Visited sets: one byte per node for each of stamp_slots warp slots (row
+    // stride stamp_stride bytes); a node is visited in the current stage when
+    // its byte equals the slot's current epoch.  stamp_epoch holds each slot's
+    // running epoch counter across launches.
+    uint8_t* stamps;
+    uint32_t* stamp_epoch;
+    int64_t stamp_stride;
+    int stamp_slots;
 };
 
 struct SearchConfig {
     int k, ef;
     int stage1, stage2_expansions, stage3, use_fes;
-    int hash_log2;
     int warps_per_block;
     int fes_T;
     int stage_bytes;     // per-warp row staging buffer
@@ -53,7 +60,7 @@ struct SearchIO {
     float* out_dists;          // nq x k
     int32_t* counters;         // nq x 8 or null
     int32_t* bad_query;        // nq flags (non-finite input)
-    int32_t* status;           // [0] non-finite queries, [1] next query, [2] hash overflows,
+    int32_t* status;           // [0] non-finite queries, [1] next query, [2] unused,
                                // [3] FES fallbacks, [4] expansion-cap hits
 };
 
@@ -63,7 +70,7 @@ cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const Sea
                           int num_sms);
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
 // The defaults of every search entry point (stages as in the paper, T = 8 FES
-// survivors, automatic visited-table and staging sizes).
+// survivors, automatic staging size).
 SearchConfig default_search_config(const DevIndex& ix, int k, int ef);
 
 // Internal view of a loaded index for entry points outside pilot_api.cu.

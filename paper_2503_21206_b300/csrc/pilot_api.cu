@@ -306,6 +306,31 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     X.red = p;
     if ((s = ix->upload_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) return s;
     X.full = static_cast<const float*>(p);
+    // visited bytes: one row of n bytes per warp slot, as many slots as the
+    // search kernel can keep resident (16 warps per SM), within a quarter of
+    // the free device memory
+    {
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        X.stamp_stride = (n + 255) / 256 * 256;
+        int64_t slots = int64_t(ix->num_sms) * 16;
+        const int64_t cap = int64_t(free_b / 4) / X.stamp_stride;
+        if (slots > cap) slots = cap;
+        if (slots < 8) return fail(PILOT_ENOMEM, "no room for the visited sets (%lld bytes per slot)",
+                                   (long long)X.stamp_stride);
+        X.stamp_slots = int(slots);
+        void* p1 = nullptr;
+        CUDA_TRY(cudaMalloc(&p1, size_t(slots) * size_t(X.stamp_stride)));
+        ix->allocs.push_back(p1);
+        CUDA_TRY(cudaMemset(p1, 0, size_t(slots) * size_t(X.stamp_stride)));
+        X.stamps = static_cast<uint8_t*>(p1);
+        void* p2 = nullptr;
+        CUDA_TRY(cudaMalloc(&p2, size_t(slots) * 4));
+        ix->allocs.push_back(p2);
+        CUDA_TRY(cudaMemset(p2, 0, size_t(slots) * 4));
+        X.stamp_epoch = static_cast<uint32_t*>(p2);
+        ix->device_bytes += size_t(slots) * size_t(X.stamp_stride) + size_t(slots) * 4;
+    }
     CUDA_TRY(cudaMallocHost(&ix->status_host, 8 * sizeof(int32_t)));
     *out = guard.release();
     return PILOT_OK;
@@ -432,8 +457,6 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cfg.stage3 = opt.stage3 != 0;
     cfg.use_fes = opt.use_fes != 0;
     if (opt.warps_per_block > 0) cfg.warps_per_block = std::min(opt.warps_per_block, 8);
-    if (opt.hash_log2 > 0) cfg.hash_log2 = opt.hash_log2;
-    if (cfg.hash_log2 < 5 || cfg.hash_log2 > 16) return fail(PILOT_EINVAL, "hash_log2 = %d out of [5, 16]", cfg.hash_log2);
 
     const bool q_dev = is_device_ptr(queries);
     const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);
@@ -494,7 +517,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
         if (e == cudaErrorInvalidConfiguration) {
             cudaGetLastError();
             return fail(PILOT_EINVAL, "per-block shared memory (%zu B per warp x %d warps) exceeds the device limit; "
-                        "lower hash_log2, ef or warps_per_block", search_smem_per_warp(X, cfg), cfg.warps_per_block);
+                        "lower ef or warps_per_block", search_smem_per_warp(X, cfg), cfg.warps_per_block);
         }
         CUDA_TRY(e);
     }

@@ -12,9 +12,12 @@
 //                 unchecked, reusing stage (2)'s visited table (Sec. 4.1 (3))
 //   output        the first k candidates by (distance, id)
 //
-// Per-warp shared memory: the candidate list C (sorted 64-bit keys, two
-// buffers for the merge), the visited hash, the query and projected query,
-// and a staging buffer for gathered rows.  Distance batches: up to 32 rows;
+// Per-warp shared memory: the candidate list C (sorted 64-bit keys), the
+// query and projected query, and a staging buffer for gathered rows.  The
+// visited sets live in HBM: one byte per node for every warp slot, tagged with
+// a per-slot epoch so that a slot is cleared only once every 255 stages.  The
+// visited bytes of an expansion's neighbours are loaded together with their
+// rows, so the check adds no dependent memory round trip.  Distance batches: up to 32 rows;
 // eight lanes cover one 128-byte line of a row (16-byte cp.async copies into
 // shared memory), each lane owns 8 rows x its chunks, and a transposing
 // shuffle reduction leaves each row's sum in one lane.  New candidates are
@@ -32,7 +35,7 @@ constexpr int kMaxExpansionsPerStage = 1 << 22;
 
 struct Layout {
     int pool_cap;      // power of two >= ef
-    int off_pool0, off_hash, off_cand, off_dist, off_bkeys, off_q, off_qp, off_stage;
+    int off_pool0, off_cand, off_dist, off_bkeys, off_q, off_qp, off_stage;
     int per_warp;
 };
 
@@ -49,7 +52,6 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
     L.pool_cap = pow2_ceil(cfg.ef < 32 ? 32 : cfg.ef);
     int o = 0;
     L.off_pool0 = o; o += L.pool_cap * 8;
-    L.off_hash = o; o += (1 << cfg.hash_log2) * 4;
     L.off_cand = o; o += kCand * 4;
     L.off_dist = o; o += kCand * 4;
     L.off_bkeys = o; o += kCand * 8;
@@ -64,7 +66,7 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
 
 struct Warp {
     uint64_t* pool;
-    uint32_t* hash;
+    uint8_t* stamps;     // this warp slot's visited bytes
     int32_t* cand;
     float* dist;
     uint64_t* bkeys;
@@ -73,8 +75,8 @@ struct Warp {
     uint8_t* stage;
     int S;          // candidates in C
     int lb;         // every candidate before position lb is checked
-    int log2h;
-    int overflow;
+    uint32_t epoch_ctr;
+    uint32_t epoch;  // 1..255: the current stage's visited tag
     int lane;
 };
 
@@ -267,6 +269,20 @@ __device__ __forceinline__ void sort_pool(Warp& w, int cap) {
     }
 }
 
+// Start a new visited set for this warp slot.  Epochs cycle through 1..255;
+// before a cycle restarts the slot's bytes are cleared.
+__device__ __forceinline__ void new_visited_set(Warp& w, int64_t stride) {
+    w.epoch_ctr += 1;
+    const uint32_t r = w.epoch_ctr % 255u;
+    if (r == 0) {
+        uint4* p = reinterpret_cast<uint4*>(w.stamps);
+        const int64_t n16 = stride >> 4;
+        for (int64_t i = w.lane; i < n16; i += 32) p[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    w.epoch = r + 1;
+    __syncwarp();
+}
+
 template <int DT, int METRIC>
 struct Searcher {
     const DevIndex& ix;
@@ -332,17 +348,23 @@ struct Searcher {
             const int j = b0 + lane;
             int32_t v = j < W ? __ldg(row + j) : -1;
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
-            const bool isnew = hash_insert_warp(w.hash, w.log2h, uint32_t(v), v >= 0, w.overflow);
-            const unsigned nb = __ballot_sync(kFull, isnew);
-            const int cnt = __popc(nb);
-            if (cnt == 0) continue;
-            if (isnew) w.cand[__popc(nb & lanemask_lt())] = v;
+            const unsigned vb = __ballot_sync(kFull, v >= 0);
+            const int m = __popc(vb);
+            if (m == 0) continue;
+            if (v >= 0) w.cand[__popc(vb & lanemask_lt())] = v;
             __syncwarp();
-            if (view == 1) reduced_batch(cnt);
-            else full_batch(cnt);
-            __syncwarp();
+            // visited bytes of all neighbours, in flight with their rows; the
+            // distance batch covers every neighbour and the visited ones are
+            // dropped afterwards
+            const int32_t mine = lane < m ? w.cand[lane] : 0;
+            const uint32_t tag = lane < m ? uint32_t(w.stamps[mine]) : w.epoch;
+            if (view == 1) reduced_batch(m);
+            else full_batch(m);
+            const bool isnew = tag != w.epoch;
+            if (isnew) w.stamps[mine] = uint8_t(w.epoch);
+            const int cnt = __popc(__ballot_sync(kFull, isnew));
             n_dist += cnt;
-            uint64_t k = lane < cnt ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
+            uint64_t k = isnew ? make_key(w.dist[lane], mine) : kKeyEmpty;
             // a full list only admits keys below its worst one
             if (w.S == cfg.ef && k >= (w.pool[w.S - 1] & ~1ull)) k = kKeyEmpty;
             const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
@@ -400,12 +422,13 @@ struct Searcher {
 
         // ---- stage (1): Algorithm 1 on the subgraph, reduced rows
         int e1 = 0, d1 = 0, e2 = 0, d2 = 0, e3 = 0, d3 = 0;
-        hash_clear(w.hash, w.log2h, lane);
-        if (lane == 0) w.pool[0] = best;
+        new_visited_set(w, ix.stamp_stride);
+        if (lane == 0) {
+            w.pool[0] = best;
+            w.stamps[key_id(best)] = uint8_t(w.epoch);
+        }
         w.S = 1;
         w.lb = 0;
-        __syncwarp();
-        hash_insert_warp(w.hash, w.log2h, uint32_t(key_id(best)), lane == 0, w.overflow);
         __syncwarp();
         bool capped = false;
         if (cfg.stage1) {
@@ -416,9 +439,7 @@ struct Searcher {
         const int n_rerank = w.S;
 
         // ---- re-rank: full distances, fresh visited table = ids(C)
-        __syncwarp();
-        hash_clear(w.hash, w.log2h, lane);
-        __syncwarp();
+        new_visited_set(w, ix.stamp_stride);
         for (int b0 = 0; b0 < w.S; b0 += kCand) {
             const int m = min(kCand, w.S - b0);
             int32_t orig = -1;
@@ -429,8 +450,10 @@ struct Searcher {
             __syncwarp();
             full_batch(m);
             __syncwarp();
-            if (lane < m) w.pool[b0 + lane] = make_key(w.dist[lane], orig);
-            hash_insert_warp(w.hash, w.log2h, uint32_t(orig), lane < m, w.overflow);
+            if (lane < m) {
+                w.pool[b0 + lane] = make_key(w.dist[lane], orig);
+                w.stamps[orig] = uint8_t(w.epoch);
+            }
             __syncwarp();
         }
         sort_pool(w, 0x7FFFFFFF);
@@ -477,15 +500,16 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
     uint8_t* base = smem + size_t(warp) * L.per_warp;
     Warp w;
     w.pool = reinterpret_cast<uint64_t*>(base + L.off_pool0);
-    w.hash = reinterpret_cast<uint32_t*>(base + L.off_hash);
+    const int slot = blockIdx.x * cfg.warps_per_block + warp;   // < ix.stamp_slots (launch bound)
+    w.stamps = ix.stamps + int64_t(slot) * ix.stamp_stride;
+    w.epoch_ctr = ix.stamp_epoch[slot];
+    w.epoch = 0;
     w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
     w.dist = reinterpret_cast<float*>(base + L.off_dist);
     w.bkeys = reinterpret_cast<uint64_t*>(base + L.off_bkeys);
     w.q = reinterpret_cast<float*>(base + L.off_q);
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
     w.stage = base + L.off_stage;
-    w.log2h = cfg.hash_log2;
-    w.overflow = 0;
     w.lane = threadIdx.x & 31;
     w.S = 0;
     w.lb = 0;
@@ -504,7 +528,7 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
         }
         s.run(q, io, io.counters);
     }
-    if (w.lane == 0 && w.overflow) atomicAdd(&io.status[2], w.overflow);
+    if (w.lane == 0) ix.stamp_epoch[slot] = w.epoch_ctr;
 }
 
 template <int DT, int METRIC>
@@ -525,6 +549,7 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t blocks = int64_t(per_sm) * num_sms;
+    if (blocks * cfg.warps_per_block > ix.stamp_slots) blocks = ix.stamp_slots / cfg.warps_per_block;
     const int64_t need = (io.nq + cfg.warps_per_block - 1) / cfg.warps_per_block;
     if (blocks > need) blocks = need;
     if (blocks < 1) return cudaSuccess;
@@ -546,9 +571,6 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.use_fes = 1;
     cfg.fes_T = 8;
     cfg.warps_per_block = 2;
-    int hl = 10;
-    while ((1 << hl) < 8 * ef && hl < 13) ++hl;
-    cfg.hash_log2 = hl;
     int stage = 4 * (ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes);
     const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;
     stage = stage > full32 ? stage : full32;
