@@ -71,23 +71,31 @@ def aggregate_throughput(units_per_rank: int, world: int, max_seconds: float) ->
 
 # ----------------------------------------------------------------- inputs --
 
-def _cache_dir(name: str, n: int | None, nq: int | None) -> str:
+def _cache_dir(name: str, n: int | None) -> str:
     base = os.environ.get("PILOT_BENCH_CACHE", os.path.join(tempfile.gettempdir(), "pilot_bench_cache"))
-    return os.path.join(base, f"{name}_n{n or 'full'}_q{nq or 'full'}")
+    return os.path.join(base, f"{name}_n{n or 'full'}")
 
 
 def load_workload(name: str, n: int | None = None, nq: int | None = None, verbose: bool = True):
-    """(workload, index data, queries, exact top-k ids), cached on disk."""
+    """(workload, index data, queries, exact top-k ids), cached on disk.  The
+    query generator is prefix-stable, so ``nq`` takes the first nq queries."""
+    w, idx, Q, gt = _load_full(name, n, verbose)
+    if nq is not None:
+        Q, gt = Q[:nq], gt[:nq]
+    return w, idx, np.ascontiguousarray(Q), gt
+
+
+def _load_full(name: str, n: int | None, verbose: bool):
     import torch
     from paper_2503_21206_b300 import index_build, synth
     w = synth.WORKLOADS[name]
-    cdir = _cache_dir(name, n, nq)
+    cdir = _cache_dir(name, n)
     if os.path.exists(os.path.join(cdir, "done")):
         idx = index_build.load_index(cdir)
         return w, idx, np.load(os.path.join(cdir, "queries.npy")), np.load(os.path.join(cdir, "gt.npy"))
     dev = "cuda" if torch.cuda.is_available() else None
     t0 = time.time()
-    idx, Q, _, _ = index_build.build_workload(w, device=dev, n=n, nq=nq)
+    idx, Q, _, _ = index_build.build_workload(w, device=dev, n=n)
     t1 = time.time()
     gt, _ = index_build.exact_topk(idx.full, Q, w.k, metric=w.metric, device=dev)
     if verbose:

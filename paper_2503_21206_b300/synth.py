@@ -78,13 +78,17 @@ def haar_rotation(d: int, rng: np.random.Generator) -> np.ndarray:
     return q * np.sign(np.diag(r))[None, :]
 
 
-def _mixture(n: int, centres: np.ndarray, sigma: float, rng: np.random.Generator, chunk: int) -> np.ndarray:
+def _mixture(n: int, centres: np.ndarray, sigma: float, seed: int, chunk: int) -> np.ndarray:
+    """Components and noise come from separate streams, so the first m rows
+    do not depend on n (a smaller case is a prefix of a larger one)."""
     d = centres.shape[1]
+    crng = np.random.default_rng([seed, 1])
+    nrng = np.random.default_rng([seed, 2])
     out = np.empty((n, d), np.float32)
     for s in range(0, n, chunk):
         m = min(chunk, n - s)
-        comp = rng.integers(0, centres.shape[0], m)
-        out[s:s + m] = centres[comp] + sigma * rng.standard_normal((m, d))
+        comp = crng.integers(0, centres.shape[0], m)
+        out[s:s + m] = centres[comp] + sigma * nrng.standard_normal((m, d))
     return out
 
 
@@ -108,15 +112,15 @@ def generate(w: Workload, n: int | None = None, nq: int | None = None, chunk: in
     Mixture: centres ~ N(0, I), points = centre + sigma * N(0, I); queries from
     the same mixture.  Power law: z ~ N(0, diag(i^-power)), a seeded Haar
     rotation, optional unit normalisation; queries from the same law.
-    ``n`` / ``nq`` override the sizes (a prefix-stable smaller case)."""
+    ``n`` / ``nq`` override the sizes; a smaller case is a prefix of a larger one."""
     n = w.n if n is None else n
     nq = w.nq if nq is None else nq
     drng = np.random.default_rng(w.data_seed)
     qrng = np.random.default_rng(w.query_seed)
     if w.kind == "mixture":
         centres = drng.standard_normal((w.n_comp, w.d))
-        base = _mixture(n, centres, w.sigma, drng, chunk)
-        queries = _mixture(nq, centres, w.sigma, qrng, chunk)
+        base = _mixture(n, centres, w.sigma, w.data_seed, chunk)
+        queries = _mixture(nq, centres, w.sigma, w.query_seed, chunk)
     elif w.kind == "powerlaw":
         rot = haar_rotation(w.d, drng)
         base = _powerlaw(n, w.d, w.power, rot, w.unit_norm, drng, chunk)

@@ -74,9 +74,14 @@ def test_exact_topk_matches_bruteforce(c1_small):
     assert np.array_equal(a, b)
 
 
-def test_workloads_are_seeded():
+def test_workloads_are_seeded_and_prefix_stable():
     w = synth.WORKLOADS["c2_aniso_1m_d96"]
     x1, q1 = synth.generate(w, n=500, nq=10)
     x2, q2 = synth.generate(w, n=500, nq=10)
     assert np.array_equal(x1, x2) and np.array_equal(q1, q2)
     np.testing.assert_allclose(np.linalg.norm(x1, axis=1), 1.0, rtol=1e-5)
+    for name in ("c1_mixture_20k_d96", "c2_aniso_1m_d96"):
+        wl = synth.WORKLOADS[name]
+        xa, qa = synth.generate(wl, n=300, nq=20)
+        xb, qb = synth.generate(wl, n=900, nq=70)
+        assert np.array_equal(xa, xb[:300]) and np.array_equal(qa, qb[:20])
