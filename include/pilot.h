@@ -127,7 +127,8 @@ typedef struct {
     int32_t stage2_expansions;  /* stage (2) subgraph expansions (default 2, Sec. 4.1 (2)) */
     int32_t stage3;             /* 1: run stage (3) (default 1) */
     int32_t use_fes;            /* 1: FES entry (default); 0: entry_ids[0] */
-    int32_t warps_per_block;    /* 0 = automatic */
+    int32_t warps_per_block;    /* search warps (one query each) per block, 1..8; 0 = automatic */
+    int32_t stage_rows;         /* rows gathered per pass into shared memory, 4..32; 0 = automatic */
     int32_t* counters;          /* optional nq x 8 int32 (host or device): per query the
                                    expansions and distances of stages (1), (2), (3), the
                                    number of re-ranked candidates and the entry id */

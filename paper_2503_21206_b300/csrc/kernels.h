@@ -60,7 +60,7 @@ struct SearchIO {
     float* out_dists;          // nq x k
     int32_t* counters;         // nq x 8 or null
     int32_t* bad_query;        // nq flags (non-finite input)
-    int32_t* status;           // [0] non-finite queries, [1] next query, [2] unused,
+    int32_t* status;           // [0] non-finite queries, [1] next query, [2] gather timeouts,
                                // [3] FES fallbacks, [4] expansion-cap hits
 };
 
@@ -72,6 +72,8 @@ size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
 // The defaults of every search entry point (stages as in the paper, T = 8 FES
 // survivors, automatic staging size).
 SearchConfig default_search_config(const DevIndex& ix, int k, int ef);
+// Stage `rows` rows of the widest row kind per gather pass (4..32).
+void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows);
 
 // Internal view of a loaded index for entry points outside pilot_api.cu.
 struct IndexView {

@@ -153,6 +153,7 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     if ((e = cudaMemcpyAsync(v.status_host, io.status, 8 * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_error(e, "read status");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    if (v.status_host[2]) return error(PILOT_ETIMEOUT, "%lld search warps gave up waiting for a row gather", v.status_host[2]);
     if (v.status_host[4]) return error(PILOT_ECUDA, "%lld queries hit the expansion cap", v.status_host[4]);
     if (v.status_host[0])
         return error(PILOT_EINVAL, "%lld queries hold NaN or infinity (their results are -1 / +inf)",

@@ -457,6 +457,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cfg.stage3 = opt.stage3 != 0;
     cfg.use_fes = opt.use_fes != 0;
     if (opt.warps_per_block > 0) cfg.warps_per_block = std::min(opt.warps_per_block, 8);
+    if (opt.stage_rows > 0) set_stage_rows(X, cfg, opt.stage_rows);
 
     const bool q_dev = is_device_ptr(queries);
     const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);
@@ -532,6 +533,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (timed)
         for (int i = 0; i < 3; ++i) CUDA_TRY(cudaEventElapsedTime(&opt.kernel_ms[i], ix->ev[i], ix->ev[i + 1]));
     const int32_t* S = ix->status_host;
+    if (S[2]) return fail(PILOT_ETIMEOUT, "%d search warps gave up waiting for a row gather", S[2]);
     if (S[4]) return fail(PILOT_ECUDA, "%d queries hit the expansion cap", S[4]);
     if (S[0]) return fail(PILOT_EINVAL, "%d queries hold NaN or infinity (their results are -1 / +inf)", S[0]);
     return PILOT_OK;

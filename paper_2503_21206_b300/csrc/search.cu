@@ -32,10 +32,12 @@ namespace {
 
 constexpr int kCand = 32;   // distance batch (rows)
 constexpr int kMaxExpansionsPerStage = 1 << 22;
+constexpr bool kBoundedRejection = false;
+constexpr uint32_t kMaxPolls = 1u << 24;   // bound on polls of one gather's barrier
 
 struct Layout {
     int pool_cap;      // power of two >= ef
-    int off_pool0, off_cand, off_dist, off_bkeys, off_q, off_qp, off_stage;
+    int off_pool0, off_cand, off_dist, off_bar, off_sel, off_bkeys, off_q, off_qp, off_stage;
     int per_warp;
 };
 
@@ -54,6 +56,8 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
     L.off_pool0 = o; o += L.pool_cap * 8;
     L.off_cand = o; o += kCand * 4;
     L.off_dist = o; o += kCand * 4;
+    L.off_bar = o; o += 16;
+    L.off_sel = o; o += kCand * 4;
     L.off_bkeys = o; o += kCand * 8;
     o = round_up(o, 16);
     L.off_q = o; o += ix.d_pad * 4;
@@ -68,6 +72,7 @@ struct Warp {
     uint64_t* pool;
     uint8_t* stamps;     // this warp slot's visited bytes
     int32_t* cand;
+    int32_t* sel;        // staged rows that need an exact distance
     float* dist;
     uint64_t* bkeys;
     float* q;
@@ -78,114 +83,253 @@ struct Warp {
     uint32_t epoch_ctr;
     uint32_t epoch;  // 1..255: the current stage's visited tag
     int lane;
+    uint64_t* bar;      // mbarrier of this warp's row gathers
+    uint32_t phase;     // parity of the barrier phase being waited for
+    bool failed;        // a gather did not complete within kMaxPolls polls
 };
 
-// Distances of rows cand[0..m) of a row array (`base`, `row_bytes` per row,
-// element type DT: 0 f32, 1 bf16, 2 fp8 codes with per-row `scales`) to the
-// query q held in shared memory; results in dist[0..m).
+// Exact accumulation of one 16-byte chunk of a row into acc: the chunk holds
+// 4 FP32, 8 BF16 or 16 FP8 elements; qc points at the matching query elements;
+// sc is the row's FP8 scale.
 template <int DT, int METRIC>
-__device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
-                                           const float* __restrict__ scales, const float* q, int m,
-                                           int stage_bytes) {
-    const int lane = w.lane;
-    const int g = lane >> 3, mm = lane & 7;
-    const int F8 = row_bytes >> 7;   // 16-byte chunks per lane per row
-    int P = stage_bytes / row_bytes;
-    P = P >= kCand ? kCand : (P & ~3);
-    const int jrows = (m + 3) >> 2;   // row slots any lane needs (warp-uniform)
-    DF acc[8];
+__device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, float sc) {
+    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+    if (DT == 0) {
+        const float4 qv = *reinterpret_cast<const float4*>(qc);
+        const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = DF{0.0f, 0.0f};
-    for (int r0 = 0; r0 < m; r0 += P) {
+        for (int e = 0; e < 4; ++e) {
+            if (METRIC == 0) l2_acc(acc, qa[e], __uint_as_float(wv[e]));
+            else ip_acc(acc, qa[e], __uint_as_float(wv[e]));
+        }
+    } else if (DT == 1) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = g + 4 * j;
-            if (r >= r0 && r < r0 + P && r < m) {
-                const uint8_t* src = base + int64_t(w.cand[r]) * row_bytes;
-                uint8_t* dst = w.stage + (r - r0) * row_bytes;
-                for (int t = 0; t < F8; ++t) cp_async16(dst + (mm + 8 * t) * 16, src + (mm + 8 * t) * 16);
+        for (int h = 0; h < 4; ++h) {
+            const float2 qv = *reinterpret_cast<const float2*>(qc + h * 2);
+            const float x0 = bf16_to_f32(wv[h] & 0xFFFFu), x1 = bf16_to_f32(wv[h] >> 16);
+            if (METRIC == 0) {
+                l2_acc(acc, qv.x, x0);
+                l2_acc(acc, qv.y, x1);
+            } else {
+                ip_acc(acc, qv.x, x0);
+                ip_acc(acc, qv.y, x1);
             }
         }
-        cp_async_wait_all();
+    } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = g + 4 * j;
-            // every lane works on row slot j when any lane needs it (rows past m
-            // hold stale data whose result is discarded), so the warp stays converged
-            if (j < jrows && 4 * j >= r0 && 4 * j < r0 + P) {
-                const uint8_t* srow = w.stage + (r - r0) * row_bytes;
-                float sc = 1.0f;
-                if (DT == 2) sc = r < m ? __ldg(scales + w.cand[r]) : 1.0f;
-                for (int t = 0; t < F8; ++t) {
-                    const int c = mm + 8 * t;
-                    uint4 v = *reinterpret_cast<const uint4*>(srow + c * 16);
-                    if (DT == 0) {
-                        float4 qv = *reinterpret_cast<const float4*>(q + c * 4);
-                        float x[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
-                                      __uint_as_float(v.w)};
-                        float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+        for (int h = 0; h < 4; ++h) {
+            const float4 qv = *reinterpret_cast<const float4*>(qc + h * 4);
+            const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (METRIC == 0) l2_acc(acc[j], qa[e], x[e]);
-                            else ip_acc(acc[j], qa[e], x[e]);
-                        }
-                    } else if (DT == 1) {
-                        uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            float2 qv = *reinterpret_cast<const float2*>(q + c * 8 + h * 2);
-                            float x0 = bf16_to_f32(wv[h] & 0xFFFFu), x1 = bf16_to_f32(wv[h] >> 16);
-                            if (METRIC == 0) {
-                                l2_acc(acc[j], qv.x, x0);
-                                l2_acc(acc[j], qv.y, x1);
-                            } else {
-                                ip_acc(acc[j], qv.x, x0);
-                                ip_acc(acc[j], qv.y, x1);
-                            }
-                        }
-                    } else {
-                        uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            float4 qv = *reinterpret_cast<const float4*>(q + c * 16 + h * 4);
-                            float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                float xl;
-                                float xh = two_prod(e4m3_to_f32((wv[h] >> (8 * b)) & 0xFFu), sc, xl);
-                                if (METRIC == 0) l2_acc2(acc[j], qa[b], xh, xl);
-                                else ip_acc2(acc[j], qa[b], xh, xl);
-                            }
-                        }
-                    }
-                }
+            for (int b = 0; b < 4; ++b) {
+                float xl;
+                const float xh = two_prod(e4m3_to_f32((wv[h] >> (8 * b)) & 0xFFu), sc, xl);
+                if (METRIC == 0) l2_acc2(acc, qa[b], xh, xl);
+                else ip_acc2(acc, qa[b], xh, xl);
             }
         }
     }
-    // Transposing reduction over the eight lanes of a group: afterwards lane
-    // (g, mm) holds the full sum of row g + 4 * mm.
+}
+
+// Plain FP32 sum of one chunk for the rejection test (a = sum (q - x)^2 for
+// L2; a = sum q x and b = sum |q| |x| for IP).
+template <int DT, int METRIC>
+__device__ __forceinline__ void approx_chunk(float& a, float& b, uint4 v, const float* qc, float sc) {
+    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        constexpr int PER = DT == 0 ? 1 : (DT == 1 ? 2 : 4);   // elements per 32-bit word
+        float x[PER], qe[PER];
+        if (DT == 0) {
+            x[0] = __uint_as_float(wv[h]);
+        } else if (DT == 1) {
+            x[0] = bf16_to_f32(wv[h] & 0xFFFFu);
+            x[PER - 1] = bf16_to_f32(wv[h] >> 16);
+        } else {
+#pragma unroll
+            for (int e = 0; e < PER; ++e) x[e] = e4m3_to_f32((wv[h] >> (8 * e)) & 0xFFu) * sc;
+        }
+        if (DT == 0) {
+            qe[0] = qc[h];
+        } else if (DT == 1) {
+            const float2 qv = *reinterpret_cast<const float2*>(qc + 2 * h);
+            qe[0] = qv.x;
+            qe[PER - 1] = qv.y;
+        } else {
+            const float4 qv = *reinterpret_cast<const float4*>(qc + 4 * h);
+            const float t[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+            for (int e = 0; e < PER; ++e) qe[e] = t[e];
+        }
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            if (METRIC == 0) {
+                const float dd = qe[e] - x[e];
+                a = fmaf(dd, dd, a);
+            } else {
+                a = fmaf(qe[e], x[e], a);
+                b = fmaf(fabsf(qe[e]), fabsf(x[e]), b);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float reduce8f(float (&acc)[8], int mm) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const bool up = mm & 4;
-        DF send = up ? acc[i] : acc[i + 4];
-        DF keep = up ? acc[i + 4] : acc[i];
+        const float send = up ? acc[i] : acc[i + 4];
+        acc[i] = (up ? acc[i + 4] : acc[i]) + __shfl_xor_sync(kFull, send, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = mm & 2;
+        const float send = up ? acc[i] : acc[i + 2];
+        acc[i] = (up ? acc[i + 2] : acc[i]) + __shfl_xor_sync(kFull, send, 2);
+    }
+    const bool up = mm & 1;
+    const float send = up ? acc[0] : acc[1];
+    return (up ? acc[1] : acc[0]) + __shfl_xor_sync(kFull, send, 1);
+}
+
+// Transposing reduction over the eight lanes of a group: afterwards lane
+// (g, mm) holds the full sum of row slot g + 4 * mm.
+__device__ __forceinline__ DF reduce8(DF (&acc)[8], int mm) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = mm & 4;
+        const DF send = up ? acc[i] : acc[i + 4];
+        const DF keep = up ? acc[i + 4] : acc[i];
         acc[i] = df_add(keep, df_shfl_xor(send, 4));
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const bool up = mm & 2;
-        DF send = up ? acc[i] : acc[i + 2];
-        DF keep = up ? acc[i + 2] : acc[i];
+        const DF send = up ? acc[i] : acc[i + 2];
+        const DF keep = up ? acc[i + 2] : acc[i];
         acc[i] = df_add(keep, df_shfl_xor(send, 2));
     }
-    {
-        const bool up = mm & 1;
-        DF send = up ? acc[0] : acc[1];
-        DF keep = up ? acc[1] : acc[0];
-        acc[0] = df_add(keep, df_shfl_xor(send, 1));
+    const bool up = mm & 1;
+    const DF send = up ? acc[0] : acc[1];
+    const DF keep = up ? acc[1] : acc[0];
+    return df_add(keep, df_shfl_xor(send, 1));
+}
+
+// Exact distances of the staged rows sel(i), i < m, into dist[sel(i)].
+// Staged row s lives at stage + s * row_bytes.  Row slots are spread as lane
+// (g, mm) -> rows g + 4 j, chunks mm + 8 t, for a warp-uniform number of slots.
+template <int DT, int METRIC, class Sel>
+__device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float* __restrict__ scales,
+                                             const float* q, int m, Sel sel, int cand_off) {
+    const int g = w.lane >> 3, mm = w.lane & 7;
+    const int F8 = row_bytes >> 7;
+    constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
+    const int jrows = (m + 3) >> 2;
+    DF acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j] = DF{0.0f, 0.0f};
+        if (j < jrows) {
+            const int i = g + 4 * j;
+            const int srow = sel(i < m ? i : 0);
+            const uint8_t* rowp = w.stage + srow * row_bytes;
+            const float sc = DT == 2 ? __ldg(scales + w.cand[cand_off + srow]) : 1.0f;
+            for (int t = 0; t < F8; ++t) {
+                const int c = mm + 8 * t;
+                exact_chunk<DT, METRIC>(acc[j], *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
+            }
+        }
     }
+    const DF sum = reduce8(acc, mm);
+    const int i = g + 4 * mm;
+    if (i < m) w.dist[cand_off + sel(i)] = df_finish(sum, METRIC);
+}
+
+// Gather rows cand[r0..r1) (r1 - r0 <= 32) into the staging buffer: lane i
+// issues one bulk copy of row r0 + i; all complete on the warp's mbarrier.
+__device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int r0, int r1) {
+    const int n = r1 - r0;
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
+    __syncwarp();
+    if (w.lane < n)
+        bulk_copy_g2s(w.stage + w.lane * row_bytes, base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
+                      uint32_t(row_bytes), w.bar);
+    if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
+        // give the copies still in flight one more bounded wait, then report
+        mbar_wait(w.bar, w.phase, kMaxPolls);
+        w.failed = true;
+    }
+    w.phase ^= 1u;
+    __syncwarp();
+}
+
+// Exact distances of rows cand[0..m) of a row array (`base`, `row_bytes` per
+// row, element type DT: 0 f32, 1 bf16, 2 fp8 codes with per-row `scales`) to
+// the query q in shared memory, into dist[0..m).  Rows are gathered with
+// 16-byte cp.async copies, P at a time (as many as the staging buffer holds).
+template <int DT, int METRIC>
+__device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
+                                           const float* __restrict__ scales, const float* q, int m,
+                                           int stage_bytes) {
+    int P = stage_bytes / row_bytes;
+    P = P >= kCand ? kCand : (P & ~3);
+    for (int r0 = 0; r0 < m; r0 += P) {
+        const int r1 = r0 + P < m ? r0 + P : m;
+        gather_rows(w, base, row_bytes, r0, r1);
+        exact_staged<DT, METRIC>(w, row_bytes, scales, q, r1 - r0, [](int i) { return i; }, r0);
+        __syncwarp();
+    }
+}
+
+// Distances of rows cand[0..m) when the list is full and the next FP32 value
+// above its worst distance is reject_at.  Each row first gets a plain FP32 sum
+// with a rigorous rounding bound; a row whose lower bound reaches reject_at
+// has exact distance > the worst, so it cannot enter the list whatever the
+// ids, and is reported as +inf.  Only the remaining rows are computed exactly,
+// from the same staged data.  All m rows must fit in the staging buffer.  Not
+// used for FP8 rows with L2 (no simple relative bound for (q - fl(c s))^2).
+template <int DT, int METRIC>
+__device__ __forceinline__ void batch_dist_bounded(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
+                                                   const float* __restrict__ scales, const float* q, int m,
+                                                   float reject_at, int n_el) {
+    const int lane = w.lane, g = lane >> 3, mm = lane & 7;
+    const int F8 = row_bytes >> 7;
+    constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
+    gather_rows(w, base, row_bytes, 0, m);
+    const int jrows = (m + 3) >> 2;
+    float a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        a[j] = 0.0f;
+        b[j] = 0.0f;
+        if (j < jrows) {
+            const int r = g + 4 * j < m ? g + 4 * j : 0;   // slots past m reread row 0
+            const uint8_t* rowp = w.stage + r * row_bytes;
+            const float sc = DT == 2 ? __ldg(scales + w.cand[r]) : 1.0f;
+            for (int t = 0; t < F8; ++t) {
+                const int c = mm + 8 * t;
+                approx_chunk<DT, METRIC>(a[j], b[j], *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
+            }
+        }
+    }
+    const float sa = reduce8f(a, mm);
+    const float sb = METRIC == 1 ? reduce8f(b, mm) : 0.0f;
+    // (n + 16) 2^-23 covers the relative error of an n-term FMA sum of
+    // non-negative terms (and, for IP, the dot product's error relative to
+    // sum |q| |x|) with a wide margin, including this line's own rounding.
+    const float eps = float(n_el + 16) * 1.1920929e-7f;
+    const float lbv = METRIC == 0 ? sa * (1.0f - eps) : (-sa - eps * sb * 1.001f);
     const int r = g + 4 * mm;
-    if (r < m) w.dist[r] = df_finish(acc[0], METRIC);
+    const bool need = r < m && !(lbv >= reject_at);
+    if (r < m && !need) w.dist[r] = INFINITY;
+    const unsigned nb = __ballot_sync(kFull, need);
+    const int m2 = __popc(nb);
+    if (m2 == 0) return;
+    if (need) w.sel[__popc(nb & lanemask_lt())] = r;
+    __syncwarp();
+    exact_staged<DT, METRIC>(w, row_bytes, scales, q, m2, [&](int i) { return w.sel[i]; }, 0);
 }
 
 __device__ __forceinline__ uint64_t warp_min(uint64_t v) {
@@ -358,8 +502,24 @@ struct Searcher {
             // dropped afterwards
             const int32_t mine = lane < m ? w.cand[lane] : 0;
             const uint32_t tag = lane < m ? uint32_t(w.stamps[mine]) : w.epoch;
-            if (view == 1) reduced_batch(m);
-            else full_batch(m);
+            // once the list is full only rows that might enter it need exact
+            // distances (about one in ten late in a search)
+            const bool full_list = kBoundedRejection && w.S == cfg.ef;
+            const float reject_at = full_list ? nextafterf(key_dist(w.pool[w.S - 1]), INFINITY) : INFINITY;
+            if (view == 1) {
+                if (full_list && !(DT == 2 && METRIC == 0) && m * ix.red_row_bytes <= cfg.stage_bytes)
+                    batch_dist_bounded<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes,
+                                                   ix.red_scales, w.qp, m, reject_at, ix.dp_pad);
+                else
+                    reduced_batch(m);
+            } else {
+                if (full_list && m * ix.full_row_bytes <= cfg.stage_bytes)
+                    batch_dist_bounded<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes,
+                                                  nullptr, w.q, m, reject_at, ix.d_pad);
+                else
+                    full_batch(m);
+            }
+            __syncwarp();
             const bool isnew = tag != w.epoch;
             if (isnew) w.stamps[mine] = uint8_t(w.epoch);
             const int cnt = __popc(__ballot_sync(kFull, isnew));
@@ -433,7 +593,7 @@ struct Searcher {
         bool capped = false;
         if (cfg.stage1) {
             int it = 0;
-            while (expand(1, e1, d1))
+            while (!w.failed && expand(1, e1, d1))
                 if (++it >= kMaxExpansionsPerStage) { capped = true; break; }
         }
         const int n_rerank = w.S;
@@ -461,7 +621,7 @@ struct Searcher {
 
         // ---- stage (2): a fixed number of subgraph expansions, full rows
         for (int it = 0; it < cfg.stage2_expansions; ++it)
-            if (!expand(2, e2, d2)) break;
+            if (w.failed || !expand(2, e2, d2)) break;
 
         // ---- stage (3): Algorithm 1 on the full graph, all unchecked
         if (cfg.stage3) {
@@ -469,13 +629,13 @@ struct Searcher {
             w.lb = 0;
             __syncwarp();
             int it = 0;
-            while (expand(3, e3, d3))
+            while (!w.failed && expand(3, e3, d3))
                 if (++it >= kMaxExpansionsPerStage) { capped = true; break; }
         }
 
         // ---- output: first k by (distance, id)
         for (int j = lane; j < cfg.k; j += 32) {
-            const bool ok = j < w.S;
+            const bool ok = j < w.S && !w.failed;
             const uint64_t kk = ok ? w.pool[j] : kKeyEmpty;
             io.out_ids[q * cfg.k + j] = ok ? key_id(kk) : -1;
             io.out_dists[q * cfg.k + j] = ok ? key_dist(kk) : INFINITY;
@@ -506,6 +666,12 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
     w.epoch = 0;
     w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
     w.dist = reinterpret_cast<float*>(base + L.off_dist);
+    w.sel = reinterpret_cast<int32_t*>(base + L.off_sel);
+    w.bar = reinterpret_cast<uint64_t*>(base + L.off_bar);
+    w.phase = 0;
+    w.failed = false;
+    if ((threadIdx.x & 31) == 0) mbar_init(w.bar, 1);
+    __syncwarp();
     w.bkeys = reinterpret_cast<uint64_t*>(base + L.off_bkeys);
     w.q = reinterpret_cast<float*>(base + L.off_q);
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
@@ -527,6 +693,10 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
             continue;
         }
         s.run(q, io, io.counters);
+        if (w.failed) {   // a gather timed out: report and stop taking queries
+            if (w.lane == 0) atomicAdd(&io.status[2], 1);
+            break;
+        }
     }
     if (w.lane == 0) ix.stamp_epoch[slot] = w.epoch_ctr;
 }
@@ -576,6 +746,14 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     stage = stage > full32 ? stage : full32;
     cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
     return cfg;
+}
+
+void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {
+    // rows of the widest row kind staged per pass (a multiple of 4, 4..32)
+    rows = rows < 4 ? 4 : (rows > 32 ? 32 : rows & ~3);
+    const int widest = ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes;
+    int stage = rows * widest;
+    cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
 }
 
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
