@@ -79,6 +79,7 @@ struct Warp {
     float* qp;
     uint8_t* stage;
     int S;          // candidates in C
+    int ef;         // this query's list size
     int lb;         // every candidate before position lb is checked
     uint32_t epoch_ctr;
     uint32_t epoch;  // 1..255: the current stage's visited tag
@@ -413,6 +414,17 @@ __device__ __forceinline__ void sort_pool(Warp& w, int cap) {
     }
 }
 
+enum Phase : int { kStage1 = 1, kRerank = 2, kStage2 = 3, kStage3 = 4, kDone = 5 };
+
+// Resumable per-query search state (the candidate list itself is in Warp).
+struct QState {
+    int phase, it;                      // current phase; expansions in it so far
+    int e1, d1, e2, d2, e3, d3;         // expansions / distances per stage
+    int n_rerank;
+    int fallback, capped;
+    uint64_t best;                      // FES entry key (compact id)
+};
+
 // Start a new visited set for this warp slot.  Epochs cycle through 1..255;
 // before a cycle restarts the slot's bytes are cleared.
 __device__ __forceinline__ void new_visited_set(Warp& w, int64_t stride) {
@@ -504,7 +516,7 @@ struct Searcher {
             const uint32_t tag = lane < m ? uint32_t(w.stamps[mine]) : w.epoch;
             // once the list is full only rows that might enter it need exact
             // distances (about one in ten late in a search)
-            const bool full_list = kBoundedRejection && w.S == cfg.ef;
+            const bool full_list = kBoundedRejection && w.S == w.ef;
             const float reject_at = full_list ? nextafterf(key_dist(w.pool[w.S - 1]), INFINITY) : INFINITY;
             if (view == 1) {
                 if (full_list && !(DT == 2 && METRIC == 0) && m * ix.red_row_bytes <= cfg.stage_bytes)
@@ -526,28 +538,31 @@ struct Searcher {
             n_dist += cnt;
             uint64_t k = isnew ? make_key(w.dist[lane], mine) : kKeyEmpty;
             // a full list only admits keys below its worst one
-            if (w.S == cfg.ef && k >= (w.pool[w.S - 1] & ~1ull)) k = kKeyEmpty;
+            if (w.S == w.ef && k >= (w.pool[w.S - 1] & ~1ull)) k = kKeyEmpty;
             const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
             if (nkeep == 0) continue;
             k = warp_sort32(k, lane);
-            merge_new(w, k, nkeep, cfg.ef);
+            merge_new(w, k, nkeep, w.ef);
         }
         return true;
     }
 
-    __device__ void run(int64_t q, const SearchIO& io, int32_t* cnt_out) {
-        const int lane = w.lane;
-        // query rows into shared memory
-        for (int i = lane; i < ix.d_pad; i += 32) w.q[i] = io.q_pad[q * ix.d_pad + i];
-        for (int i = lane; i < ix.qp_pad; i += 32) w.qp[i] = io.qp[q * ix.qp_pad + i];
+    // Query rows into shared memory.
+    __device__ __forceinline__ void load_query(const float* q_pad, const float* qp) {
+        for (int i = w.lane; i < ix.d_pad; i += 32) w.q[i] = q_pad[i];
+        for (int i = w.lane; i < ix.qp_pad; i += 32) w.qp[i] = qp[i];
         __syncwarp();
-        int status_fallback = 0;
+    }
 
-        // ---- fast entry selection: exact check of the scoring survivors
+    // Fast entry selection: exact distances of the scoring survivors; if the
+    // best of them is not certified below the bound on all other entries,
+    // an exact scan of the whole entry set (Sec. 5, dense form).
+    __device__ void fes(QState& st, const int32_t* fes_pos, double fes_lb) {
+        const int lane = w.lane;
         uint64_t best;
         if (cfg.use_fes) {
             const int T = cfg.fes_T;
-            const int32_t p = lane < T ? io.fes_pos[q * T + lane] : -1;
+            const int32_t p = lane < T ? fes_pos[lane] : -1;
             const bool valid = p >= 0 && p < ix.n_entry;
             const unsigned vb = __ballot_sync(kFull, valid);
             const int m = __popc(vb);
@@ -556,10 +571,9 @@ struct Searcher {
             reduced_batch(m);
             __syncwarp();
             best = warp_min(lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
-            const double lb = io.fes_lb[q];
             const float dstar = key_dist(best);
-            if (!(lb >= double(nextafterf(dstar, INFINITY)))) {
-                status_fallback = 1;
+            if (!(fes_lb >= double(nextafterf(dstar, INFINITY)))) {
+                st.fallback = 1;
                 best = kKeyEmpty;
                 for (int64_t e0 = 0; e0 < ix.n_entry; e0 += kCand) {
                     const int mm = ix.n_entry - e0 < kCand ? int(ix.n_entry - e0) : kCand;
@@ -579,9 +593,8 @@ struct Searcher {
             __syncwarp();
             best = make_key(w.dist[0], w.cand[0]);
         }
-
-        // ---- stage (1): Algorithm 1 on the subgraph, reduced rows
-        int e1 = 0, d1 = 0, e2 = 0, d2 = 0, e3 = 0, d3 = 0;
+        st.best = best;
+        // stage (1) starts from the entry alone, visited = {entry}
         new_visited_set(w, ix.stamp_stride);
         if (lane == 0) {
             w.pool[0] = best;
@@ -589,16 +602,15 @@ struct Searcher {
         }
         w.S = 1;
         w.lb = 0;
+        st.phase = kStage1;
+        st.it = 0;
         __syncwarp();
-        bool capped = false;
-        if (cfg.stage1) {
-            int it = 0;
-            while (!w.failed && expand(1, e1, d1))
-                if (++it >= kMaxExpansionsPerStage) { capped = true; break; }
-        }
-        const int n_rerank = w.S;
+    }
 
-        // ---- re-rank: full distances, fresh visited table = ids(C)
+    // Re-rank (stage (2), first part): full distances of stage (1)'s
+    // candidates, a fresh visited set holding exactly their ids, C sorted.
+    __device__ void rerank() {
+        const int lane = w.lane;
         new_visited_set(w, ix.stamp_stride);
         for (int b0 = 0; b0 < w.S; b0 += kCand) {
             const int m = min(kCand, w.S - b0);
@@ -618,36 +630,83 @@ struct Searcher {
         }
         sort_pool(w, 0x7FFFFFFF);
         w.lb = 0;
+    }
 
-        // ---- stage (2): a fixed number of subgraph expansions, full rows
-        for (int it = 0; it < cfg.stage2_expansions; ++it)
-            if (w.failed || !expand(2, e2, d2)) break;
-
-        // ---- stage (3): Algorithm 1 on the full graph, all unchecked
-        if (cfg.stage3) {
-            for (int i = lane; i < w.S; i += 32) w.pool[i] &= ~1ull;
-            w.lb = 0;
-            __syncwarp();
-            int it = 0;
-            while (!w.failed && expand(3, e3, d3))
-                if (++it >= kMaxExpansionsPerStage) { capped = true; break; }
+    // Run the staged search from its current phase for at most `budget`
+    // expansions (Sec. 4.1 stages (1)-(3); Algorithm 1 in each).
+    __device__ void advance(QState& st, int budget) {
+        while (!w.failed && st.phase != kDone) {
+            if (st.phase == kStage1) {
+                if (!cfg.stage1 || !expand(1, st.e1, st.d1)) {
+                    st.n_rerank = w.S;
+                    st.phase = kRerank;
+                } else {
+                    if (++st.it >= kMaxExpansionsPerStage) {
+                        st.capped = 1;
+                        st.n_rerank = w.S;
+                        st.phase = kRerank;
+                    }
+                    if (--budget <= 0) break;
+                }
+            } else if (st.phase == kRerank) {
+                rerank();
+                st.phase = kStage2;
+                st.it = 0;
+            } else if (st.phase == kStage2) {
+                if (st.it >= cfg.stage2_expansions || !expand(2, st.e2, st.d2)) {
+                    if (cfg.stage3) {   // stage (3): every candidate unchecked on the full graph
+                        for (int i = w.lane; i < w.S; i += 32) w.pool[i] &= ~1ull;
+                        w.lb = 0;
+                        __syncwarp();
+                        st.phase = kStage3;
+                    } else {
+                        st.phase = kDone;
+                    }
+                    st.it = 0;
+                } else {
+                    ++st.it;
+                    if (--budget <= 0) break;
+                }
+            } else {   // kStage3
+                if (!expand(3, st.e3, st.d3)) {
+                    st.phase = kDone;
+                } else {
+                    if (++st.it >= kMaxExpansionsPerStage) {
+                        st.capped = 1;
+                        st.phase = kDone;
+                    }
+                    if (--budget <= 0) break;
+                }
+            }
         }
+    }
 
-        // ---- output: first k by (distance, id)
-        for (int j = lane; j < cfg.k; j += 32) {
+    // The first k candidates by (distance, id), padded with -1 / +inf.
+    __device__ void write_output(const QState& st, int k, int32_t* ids, float* dists, int32_t* counters) {
+        for (int j = w.lane; j < k; j += 32) {
             const bool ok = j < w.S && !w.failed;
             const uint64_t kk = ok ? w.pool[j] : kKeyEmpty;
-            io.out_ids[q * cfg.k + j] = ok ? key_id(kk) : -1;
-            io.out_dists[q * cfg.k + j] = ok ? key_dist(kk) : INFINITY;
+            ids[j] = ok ? key_id(kk) : -1;
+            dists[j] = ok ? key_dist(kk) : INFINITY;
         }
-        if (lane == 0) {
-            if (cnt_out) {
-                int32_t* c = cnt_out + q * 8;
-                c[0] = e1; c[1] = d1; c[2] = e2; c[3] = d2; c[4] = e3; c[5] = d3; c[6] = n_rerank;
-                c[7] = __ldg(ix.sub2full + key_id(best));
-            }
-            if (status_fallback) atomicAdd(&io.status[3], 1);
-            if (capped) atomicAdd(&io.status[4], 1);
+        if (w.lane == 0 && counters) {
+            counters[0] = st.e1; counters[1] = st.d1; counters[2] = st.e2; counters[3] = st.d2;
+            counters[4] = st.e3; counters[5] = st.d3; counters[6] = st.n_rerank;
+            counters[7] = __ldg(ix.sub2full + key_id(st.best));
+        }
+    }
+
+    __device__ void run(int64_t q, const SearchIO& io) {
+        load_query(io.q_pad + q * ix.d_pad, io.qp + q * ix.qp_pad);
+        QState st{};
+        w.ef = cfg.ef;
+        fes(st, io.fes_pos + q * cfg.fes_T, io.fes_lb[q]);
+        advance(st, 0x7FFFFFFF);
+        write_output(st, cfg.k, io.out_ids + q * cfg.k, io.out_dists + q * cfg.k,
+                     io.counters ? io.counters + q * 8 : nullptr);
+        if (w.lane == 0) {
+            if (st.fallback) atomicAdd(&io.status[3], 1);
+            if (st.capped) atomicAdd(&io.status[4], 1);
         }
         __syncwarp();
     }
@@ -692,7 +751,7 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
             }
             continue;
         }
-        s.run(q, io, io.counters);
+        s.run(q, io);
         if (w.failed) {   // a gather timed out: report and stop taking queries
             if (w.lane == 0) atomicAdd(&io.status[2], 1);
             break;
