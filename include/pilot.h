@@ -178,6 +178,55 @@ pilot_status pilot_search_ex(pilot_index* index, const float* queries, int64_t n
 pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int64_t nq, int k, int ef,
                                   int32_t* out_ids, float* out_dists, void* stream);
 
+/*
+ * Serving (continuous batching).  A server owns device state for `slots`
+ * requests in flight and runs steps on a background thread: each step admits
+ * queued requests into free slots, then advances every request in flight by
+ * at most expansions_per_step expansions of the staged search in one
+ * persistent launch replayed from a CUDA graph; a request's candidate list,
+ * visited bytes and phase stay in device memory between steps.  Requests
+ * that arrive while others run join at the next step.  Each request's result
+ * equals pilot_search's for the same query, k and ef.
+ *
+ * Admission: ef <= max_ef (the step kernel's shared memory is sized for
+ * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
+ * max_slots or what hbm_budget_bytes holds (list, query rows and one visited
+ * byte per node per slot), whichever is smaller; further requests queue, and
+ * submit returns PILOT_EBUSY when queue_capacity requests are waiting.
+ */
+typedef struct {
+    int32_t max_slots;            /* requests in flight at most (default 4096) */
+    int32_t max_ef;               /* largest ef a request may use (default 512) */
+    int32_t max_k;                /* largest k (default 100) */
+    int32_t expansions_per_step;  /* per request per step (default 64) */
+    int32_t max_new_per_step;     /* admissions per step (default 1024) */
+    int32_t step_timeout_ms;      /* a step longer than this fails the server (default 10000) */
+    int64_t queue_capacity;       /* waiting requests before PILOT_EBUSY (default 2^20) */
+    int64_t hbm_budget_bytes;     /* device memory for slots; 0 = a quarter of free memory */
+} pilot_serve_config;
+
+typedef struct {
+    uint64_t submitted, admitted, rejected, completed, steps;
+    int32_t slots, in_flight, queued, reserved;
+    double qps;                   /* completed / (last completion - first submission) */
+    double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency */
+} pilot_serve_statistics;
+
+void pilot_serve_config_default(pilot_serve_config* config);
+/* Start a server on a loaded index (the index must outlive it). */
+pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* config, pilot_server** out);
+/* Queue one query (d floats, host memory, copied); *ticket identifies it.
+ * PILOT_EINVAL for k / ef outside the admission limits or a non-finite
+ * value; PILOT_EBUSY when the queue is full. */
+pilot_status pilot_serve_submit(pilot_server* server, const float* query, int k, int ef, uint64_t* ticket);
+/* Wait up to timeout_ms for a ticket; on success write k ids and distances
+ * (host memory).  PILOT_ETIMEOUT if not done in time (the ticket stays
+ * valid); each finished ticket can be collected once. */
+pilot_status pilot_serve_wait(pilot_server* server, uint64_t ticket, int timeout_ms, int32_t* ids, float* dists);
+pilot_status pilot_serve_stats(pilot_server* server, pilot_serve_statistics* stats);
+/* Stop the background thread and free the server (pending tickets are lost). */
+void pilot_serve_destroy(pilot_server* server);
+
 /* The calling thread's last error message ("" if none). */
 const char* pilot_last_error(void);
 

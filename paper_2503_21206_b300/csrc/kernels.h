@@ -64,6 +64,52 @@ struct SearchIO {
                                // [3] FES fallbacks, [4] expansion-cap hits
 };
 
+// ------------------------------------------------------------- serving --
+
+// One request in a serving step: its slot, and for a request admitted in
+// this step its row in the step's new-request buffers (else -1).
+struct ServeEntry {
+    int32_t slot, new_idx, k, ef;
+};
+
+// A slot's search state, kept in device memory between steps.
+struct SlotState {
+    int32_t phase, it, e1, d1, e2, d2, e3, d3, n_rerank, fallback, capped;
+    int32_t S, lb, ef, k, pad;
+    uint32_t epoch_ctr, epoch;
+    uint64_t best;
+};
+
+struct ServeIO {
+    const ServeEntry* entries;   // n_active entries (host-mapped)
+    const int32_t* n_active;     // host-mapped
+    int32_t* next;               // device counter, zeroed before each step
+    SlotState* state;            // per slot
+    uint64_t* pool;              // per slot, pool_stride keys
+    int pool_stride;
+    float* q_pad;                // per slot, d_pad floats
+    float* qp;                   // per slot, qp_pad floats
+    const float* new_q_pad;      // this step's new requests (dense rows)
+    const float* new_qp;
+    const int32_t* new_fes_pos;
+    const double* new_fes_lb;
+    uint8_t* stamps;             // per slot, stamp_stride bytes
+    int32_t* res_ids;            // per slot, k_max (host-mapped)
+    float* res_dists;            // per slot, k_max (host-mapped)
+    int32_t* res_done;           // per slot: 1 done, 2 failed (host-mapped)
+    int32_t* res_counters;       // per slot, 8 (host-mapped)
+    int k_max;
+    int budget;                  // expansions per slot per step
+};
+
+// Set the step kernel's attributes and size its grid (call outside capture).
+cudaError_t prepare_serve_step(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
+                               size_t* smem);
+// Launch one step (capturable).
+cudaError_t launch_serve_step(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
+                              int blocks, size_t smem);
+size_t serve_smem_per_block(const DevIndex& ix, const SearchConfig& cfg);
+
 cudaError_t launch_project(const DevIndex& ix, const SearchIO& io, cudaStream_t st);
 cudaError_t launch_fes_scores(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st);
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,

@@ -712,32 +712,40 @@ struct Searcher {
     }
 };
 
-template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig cfg, SearchIO io, Layout L) {
-    extern __shared__ __align__(128) uint8_t smem[];
+// Carve this warp's slice of shared memory and initialise its barrier.
+__device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem) {
     const int warp = threadIdx.x >> 5;
     uint8_t* base = smem + size_t(warp) * L.per_warp;
     Warp w;
     w.pool = reinterpret_cast<uint64_t*>(base + L.off_pool0);
-    const int slot = blockIdx.x * cfg.warps_per_block + warp;   // < ix.stamp_slots (launch bound)
-    w.stamps = ix.stamps + int64_t(slot) * ix.stamp_stride;
-    w.epoch_ctr = ix.stamp_epoch[slot];
-    w.epoch = 0;
     w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
     w.dist = reinterpret_cast<float*>(base + L.off_dist);
     w.sel = reinterpret_cast<int32_t*>(base + L.off_sel);
     w.bar = reinterpret_cast<uint64_t*>(base + L.off_bar);
-    w.phase = 0;
-    w.failed = false;
-    if ((threadIdx.x & 31) == 0) mbar_init(w.bar, 1);
-    __syncwarp();
     w.bkeys = reinterpret_cast<uint64_t*>(base + L.off_bkeys);
     w.q = reinterpret_cast<float*>(base + L.off_q);
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
     w.stage = base + L.off_stage;
+    w.phase = 0;
+    w.failed = false;
     w.lane = threadIdx.x & 31;
     w.S = 0;
     w.lb = 0;
+    w.ef = 0;
+    w.epoch = 0;
+    w.epoch_ctr = 0;
+    if (w.lane == 0) mbar_init(w.bar, 1);
+    __syncwarp();
+    return w;
+}
+
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig cfg, SearchIO io, Layout L) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    Warp w = setup_warp(L, smem);
+    const int slot = blockIdx.x * cfg.warps_per_block + (threadIdx.x >> 5);   // < ix.stamp_slots (launch bound)
+    w.stamps = ix.stamps + int64_t(slot) * ix.stamp_stride;
+    w.epoch_ctr = ix.stamp_epoch[slot];
     Searcher<DT, METRIC> s{ix, cfg, w};
     for (;;) {
         int64_t q = 0;
@@ -758,6 +766,79 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
         }
     }
     if (w.lane == 0) ix.stamp_epoch[slot] = w.epoch_ctr;
+}
+
+// One serving step: every active request advances by at most sio.budget
+// expansions.  A request admitted in this step starts with FES (its
+// projection and FES scores were computed for the step's new rows); others
+// resume from their slot.  Finished requests write their top-k to the
+// host-mapped result rows and raise their done flag.
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConfig cfg, ServeIO sio, Layout L) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    Warp w = setup_warp(L, smem);
+    Searcher<DT, METRIC> s{ix, cfg, w};
+    const int n_active = *reinterpret_cast<const volatile int32_t*>(sio.n_active);
+    for (;;) {
+        int i = 0;
+        if (w.lane == 0) i = atomicAdd(sio.next, 1);
+        i = __shfl_sync(kFull, i, 0);
+        if (i >= n_active) break;
+        const ServeEntry e = sio.entries[i];
+        SlotState* ss = sio.state + e.slot;
+        uint64_t* gpool = sio.pool + int64_t(e.slot) * sio.pool_stride;
+        float* sq = sio.q_pad + int64_t(e.slot) * ix.d_pad;
+        float* sqp = sio.qp + int64_t(e.slot) * ix.qp_pad;
+        w.stamps = sio.stamps + int64_t(e.slot) * ix.stamp_stride;
+        w.failed = false;
+        QState st{};
+        int k;
+        if (e.new_idx >= 0) {
+            const float* nq = sio.new_q_pad + int64_t(e.new_idx) * ix.d_pad;
+            const float* nqp = sio.new_qp + int64_t(e.new_idx) * ix.qp_pad;
+            for (int j = w.lane; j < ix.d_pad; j += 32) sq[j] = nq[j];
+            for (int j = w.lane; j < ix.qp_pad; j += 32) sqp[j] = nqp[j];
+            s.load_query(nq, nqp);
+            w.epoch_ctr = ss->epoch_ctr;
+            w.ef = e.ef;
+            k = e.k;
+            s.fes(st, sio.new_fes_pos + int64_t(e.new_idx) * cfg.fes_T, sio.new_fes_lb[e.new_idx]);
+        } else {
+            s.load_query(sq, sqp);
+            st.phase = ss->phase; st.it = ss->it;
+            st.e1 = ss->e1; st.d1 = ss->d1; st.e2 = ss->e2; st.d2 = ss->d2; st.e3 = ss->e3; st.d3 = ss->d3;
+            st.n_rerank = ss->n_rerank; st.fallback = ss->fallback; st.capped = ss->capped; st.best = ss->best;
+            w.S = ss->S;
+            w.lb = ss->lb;
+            w.ef = ss->ef;
+            w.epoch_ctr = ss->epoch_ctr;
+            w.epoch = ss->epoch;
+            k = ss->k;
+            for (int j = w.lane; j < w.S; j += 32) w.pool[j] = gpool[j];
+            __syncwarp();
+        }
+        s.advance(st, sio.budget);
+        if (st.phase == kDone || w.failed) {
+            s.write_output(st, k, sio.res_ids + int64_t(e.slot) * sio.k_max,
+                           sio.res_dists + int64_t(e.slot) * sio.k_max, sio.res_counters + int64_t(e.slot) * 8);
+            __syncwarp();
+            __threadfence_system();
+            if (w.lane == 0) {
+                ss->epoch_ctr = w.epoch_ctr;
+                sio.res_done[e.slot] = w.failed ? 2 : 1;
+            }
+        } else {
+            for (int j = w.lane; j < w.S; j += 32) gpool[j] = w.pool[j];
+            if (w.lane == 0) {
+                ss->phase = st.phase; ss->it = st.it;
+                ss->e1 = st.e1; ss->d1 = st.d1; ss->e2 = st.e2; ss->d2 = st.d2; ss->e3 = st.e3; ss->d3 = st.d3;
+                ss->n_rerank = st.n_rerank; ss->fallback = st.fallback; ss->capped = st.capped; ss->best = st.best;
+                ss->S = w.S; ss->lb = w.lb; ss->ef = w.ef; ss->k = k;
+                ss->epoch_ctr = w.epoch_ctr; ss->epoch = w.epoch;
+            }
+        }
+        __syncwarp();
+    }
 }
 
 template <int DT, int METRIC>
@@ -786,7 +867,69 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO
     return cudaGetLastError();
 }
 
+template <int DT, int METRIC>
+cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
+                            size_t* smem_out) {
+    const Layout L = make_layout(ix, cfg);
+    const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(serve_step_kernel<DT, METRIC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_step_kernel<DT, METRIC>,
+                                                      cfg.warps_per_block * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t b = int64_t(per_sm) * num_sms;
+    const int64_t need = (max_warps + cfg.warps_per_block - 1) / cfg.warps_per_block;
+    *blocks = int(b > need ? need : b);
+    *smem_out = smem;
+    return cudaSuccess;
+}
+
+template <int DT, int METRIC>
+cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
+                           int blocks, size_t smem) {
+    serve_step_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, sio,
+                                                                                           make_layout(ix, cfg));
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t serve_smem_per_block(const DevIndex& ix, const SearchConfig& cfg) {
+    return make_layout(ix, cfg).per_warp * size_t(cfg.warps_per_block);
+}
+
+cudaError_t prepare_serve_step(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
+                               size_t* smem) {
+    switch (ix.red_dtype * 2 + ix.metric) {
+        case 0: return serve_prepare_t<0, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 1: return serve_prepare_t<0, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 2: return serve_prepare_t<1, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 3: return serve_prepare_t<1, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 4: return serve_prepare_t<2, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 5: return serve_prepare_t<2, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_serve_step(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
+                              int blocks, size_t smem) {
+    switch (ix.red_dtype * 2 + ix.metric) {
+        case 0: return serve_launch_t<0, 0>(ix, cfg, sio, st, blocks, smem);
+        case 1: return serve_launch_t<0, 1>(ix, cfg, sio, st, blocks, smem);
+        case 2: return serve_launch_t<1, 0>(ix, cfg, sio, st, blocks, smem);
+        case 3: return serve_launch_t<1, 1>(ix, cfg, sio, st, blocks, smem);
+        case 4: return serve_launch_t<2, 0>(ix, cfg, sio, st, blocks, smem);
+        case 5: return serve_launch_t<2, 1>(ix, cfg, sio, st, blocks, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg) { return make_layout(ix, cfg).per_warp; }
 

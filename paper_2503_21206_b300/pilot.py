@@ -208,3 +208,97 @@ def pilot_search_noalloc(index: PilotIndex, queries, k: int, ef: int, out_ids, o
     _check(_lib.pilot_search_noalloc(index.handle, _addr(queries), int(queries.shape[0]), k, ef, _addr(out_ids),
                                      _addr(out_dists), s))
     return out_ids, out_dists
+
+
+# ---------------------------------------------------------------- serving --
+
+class pilot_serve_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_ef", ctypes.c_int32), ("max_k", ctypes.c_int32),
+                ("expansions_per_step", ctypes.c_int32), ("max_new_per_step", ctypes.c_int32),
+                ("step_timeout_ms", ctypes.c_int32), ("queue_capacity", ctypes.c_int64),
+                ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class pilot_serve_statistics(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("slots", ctypes.c_int32),
+                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("qps", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double)]
+
+
+_lib.pilot_serve_config_default.argtypes = [ctypes.POINTER(pilot_serve_config)]
+_lib.pilot_serve_config_default.restype = None
+_lib.pilot_serve_create.argtypes = [_P, ctypes.POINTER(pilot_serve_config), ctypes.POINTER(_P)]
+_lib.pilot_serve_submit.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+_lib.pilot_serve_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]
+_lib.pilot_serve_stats.argtypes = [_P, ctypes.POINTER(pilot_serve_statistics)]
+_lib.pilot_serve_destroy.argtypes = [_P]
+_lib.pilot_serve_destroy.restype = None
+
+
+def pilot_serve_config_default() -> pilot_serve_config:
+    c = pilot_serve_config()
+    _lib.pilot_serve_config_default(ctypes.byref(c))
+    return c
+
+
+class PilotServer:
+    """Owns a pilot_server handle (continuous-batching search on the GPU)."""
+
+    def __init__(self, handle: int, index: PilotIndex):
+        self._h = ctypes.c_void_p(handle)
+        self._index = index   # keep the index alive while the server runs
+
+    def submit(self, query, k: int, ef: int) -> int:
+        q = np.ascontiguousarray(query, np.float32)
+        t = ctypes.c_uint64()
+        _check(_lib.pilot_serve_submit(self._h, q.ctypes.data, k, ef, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, k: int, timeout_ms: int = 60_000):
+        ids = np.empty(k, np.int32)
+        dists = np.empty(k, np.float32)
+        _check(_lib.pilot_serve_wait(self._h, ticket, timeout_ms, ids.ctypes.data, dists.ctypes.data))
+        return ids, dists
+
+    def stats(self) -> dict:
+        s = pilot_serve_statistics()
+        _check(_lib.pilot_serve_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in pilot_serve_statistics._fields_ if name != "reserved"}
+
+    def destroy(self):
+        if self._h:
+            _lib.pilot_serve_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pilot_serve_create(index: PilotIndex, config: pilot_serve_config | None = None, **overrides) -> PilotServer:
+    c = config if config is not None else pilot_serve_config_default()
+    for key, v in overrides.items():
+        setattr(c, key, v)
+    h = _P()
+    _check(_lib.pilot_serve_create(index.handle, ctypes.byref(c), ctypes.byref(h)))
+    return PilotServer(h.value, index)
+
+
+def pilot_serve_submit(server: PilotServer, query, k: int, ef: int) -> int:
+    return server.submit(query, k, ef)
+
+
+def pilot_serve_wait(server: PilotServer, ticket: int, k: int, timeout_ms: int = 60_000):
+    return server.wait(ticket, k, timeout_ms)
+
+
+def pilot_serve_stats(server: PilotServer) -> dict:
+    return server.stats()
+
+
+def pilot_serve_destroy(server: PilotServer) -> None:
+    server.destroy()

@@ -36,8 +36,6 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_mirrors_the_header(lib):
     for name in _declared():
-        if name.startswith("pilot_serve_"):
-            continue
         assert hasattr(lib, name), name
 
 
