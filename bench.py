@@ -227,6 +227,43 @@ def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q:
 
 # ------------------------------------------------------------------ arms --
 
+def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, **cfg) -> dict:
+    """Poisson arrivals at `rate` requests/s of n_req requests with k drawn
+    from {1, 10, 100} and ef uniform in 32..512 (ef >= k), submitted from this
+    thread as their arrival times pass; returns the server's statistics and
+    recall@min(k, 10) of the answers."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    ks = rng.choice([1, 10, 100], size=n_req)
+    efs = np.array([int(rng.integers(max(32, k), 513)) for k in ks])
+    rows = rng.integers(0, len(Q), n_req)
+    srv = pilot.pilot_serve_create(g, **cfg)
+    tickets = []
+    try:
+        t0 = time.perf_counter()
+        i = 0
+        while i < n_req:
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                tickets.append(srv.submit(Q[rows[i]], int(ks[i]), int(efs[i])))
+                i += 1
+            if i < n_req:
+                time.sleep(max(0.0, min(1e-4, arrivals[i] - now)))
+        hits = tot = 0
+        for j, t in enumerate(tickets):
+            ids, _ = srv.wait(t, int(ks[j]))
+            kk = min(int(ks[j]), 10)
+            hits += len(set(ids[:kk].tolist()) & set(gt[rows[j], :kk].tolist()))
+            tot += kk
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    return {"offered_rate": rate, "requests": n_req, "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
+            "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3), "slots": st["slots"],
+            "steps": st["steps"], "recall@min(k,10)": round(hits / tot, 5), "mean_ef": float(efs.mean()),
+            "k_mix": "1/10/100 uniform", "ef_mix": "uniform 32..512, ef >= k"}
+
+
 def run_reference(args):
     """The oracle as the reference arm: same workload, metric and ef rule."""
     ws, rank, _ = dist_env()
@@ -293,6 +330,8 @@ def run_pilot(args):
     opts = pilot.pilot_search_options_default()
     if args.warps_per_block:
         opts.warps_per_block = args.warps_per_block
+    if args.stage_rows:
+        opts.stage_rows = args.stage_rows
 
     def search(q, ef, o_ids, o_d, counters=None, timing=kms):
         return pilot.pilot_search_ex(g, q, k, ef, o_ids, o_d, stream, options=opts, counters=counters,
@@ -357,6 +396,10 @@ def run_pilot(args):
     e2e_value = aggregate_throughput(nq * len(e2e_s), ws, reduce_max(sum(e2e_s), device))
     e2e_recall = recall_at_k(ids_h.numpy(), gt, k)
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_run(pilot, g, Q, gt, args.serve_rate, args.serve_requests, max_ef=512, max_k=100,
+                              expansions_per_step=args.serve_budget)
     peak, peak_kind = measured_peaks()
     mean_search_ms = statistics.mean(search_ms)
     achieved = alg_bytes / (mean_search_ms / 1000.0) / 1e9
@@ -391,6 +434,8 @@ def run_pilot(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
     return 0
 
@@ -406,7 +451,12 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=None, help="smaller base set (profiling cases)")
     ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling cases)")
     ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--stage-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) run")
+    ap.add_argument("--serve-rate", type=float, default=50_000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-requests", type=int, default=100_000)
+    ap.add_argument("--serve-budget", type=int, default=128, help="expansions per request per step")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
