@@ -135,6 +135,9 @@ typedef struct {
     float* kernel_ms;           /* optional HOST array of 3 floats: device time in ms of the
                                    projection, FES scoring and search kernels of this call,
                                    from CUDA events recorded on the call's stream */
+    int32_t* status_words;      /* optional HOST array of 8 int32: [3] = queries whose FES
+                                   survivors were not certified (the entry set was scanned
+                                   exactly), [0] = non-finite queries; others reserved */
 } pilot_search_options;
 
 void pilot_search_options_default(pilot_search_options* opt);

@@ -6,6 +6,8 @@
 
 namespace pilot {
 
+constexpr int kFesT = 16;   // FES survivors per query
+
 // Device-resident index (library-owned).  Rows are padded with zeros to a
 // multiple of 128 bytes so that eight lanes cover one 128-byte line.
 struct DevIndex {
@@ -27,9 +29,9 @@ struct DevIndex {
     const float* full;         // n x d_pad
     const float2* basis;       // d x qp_pad, (hi, lo) FP32 pair of each FP64 basis value
     const int32_t* entry;      // n_entry compact ids
-    const float* entry_f32;    // n_entry x qp_pad, exact decoded reduced rows of the entries
-    const float* entry_norm2;  // n_entry, ||e||^2 (FP32 of the FP64 value)
+    const float* entry_norm2;  // ||e||^2 (FP32 of the FP64 value), +inf past n_entry to whole 256-entry tiles
     float entry_max_norm;      // max ||e||
+    const uint16_t* entry_bf16;   // entries as BF16, 256-row tiles in the UMMA K-major core-matrix layout
     // Visited sets: one byte per node for each of stamp_slots warp slots (row
     // stride stamp_stride bytes); a node is visited in the current stage when
     // its byte equals the slot's current epoch.  stamp_epoch holds each slot's
@@ -54,6 +56,7 @@ struct SearchIO {
     int64_t nq;
     float* q_pad;              // nq x d_pad
     float* qp;                 // nq x qp_pad
+    uint16_t* qp_bf16;         // q' as BF16, 128-row tiles in the UMMA K-major core-matrix layout
     int32_t* fes_pos;          // nq x fes_T entry positions
     double* fes_lb;            // nq lower bound on excluded entries' distances
     int32_t* out_ids;          // nq x k
@@ -61,7 +64,7 @@ struct SearchIO {
     int32_t* counters;         // nq x 8 or null
     int32_t* bad_query;        // nq flags (non-finite input)
     int32_t* status;           // [0] non-finite queries, [1] next query, [2] gather timeouts,
-                               // [3] FES fallbacks, [4] expansion-cap hits
+                               // [3] FES fallbacks, [4] expansion-cap hits, [5] FES kernel timeouts
 };
 
 // ------------------------------------------------------------- serving --
@@ -111,7 +114,16 @@ cudaError_t launch_serve_step(const DevIndex& ix, const SearchConfig& cfg, const
 size_t serve_smem_per_block(const DevIndex& ix, const SearchConfig& cfg);
 
 cudaError_t launch_project(const DevIndex& ix, const SearchIO& io, cudaStream_t st);
-cudaError_t launch_fes_scores(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st);
+cudaError_t launch_fes_mma(const DevIndex& ix, const SearchIO& io, cudaStream_t st);
+
+// Element offset of (row, col) in a tile-blocked UMMA K-major operand with
+// `tile_rows`-row tiles and kp columns: 8 x 8 core matrices, K-adjacent ones 64
+// elements apart, 8-row groups kp * 8 elements apart.
+__host__ __device__ inline int64_t umma_kmajor_offset(int64_t row, int col, int tile_rows, int kp) {
+    const int64_t t = row / tile_rows;
+    const int r = int(row % tile_rows);
+    return t * int64_t(tile_rows) * kp + int64_t(r >> 3) * (kp * 8) + (col >> 3) * 64 + (r & 7) * 8 + (col & 7);
+}
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
                           int num_sms);
 size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);

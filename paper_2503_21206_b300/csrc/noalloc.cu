@@ -111,10 +111,11 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     const size_t o_qpad = take(size_t(nq) * X.d_pad * 4);
     const size_t o_qp = take(size_t(nq) * X.qp_pad * 4);
     const size_t o_pos = take(size_t(nq) * cfg.fes_T * 4);
+    const size_t o_qpb = take(size_t((nq + 127) / 128 * 128) * X.qp_pad * 2);
     const size_t o_lb = take(size_t(nq) * 8);
     const size_t o_bad = take(size_t(nq) * 4);
     if (off > PILOT_NOALLOC_SCRATCH_BYTES) {
-        const size_t per_q = size_t(X.d_pad) * 4 + size_t(X.qp_pad) * 4 + size_t(cfg.fes_T) * 4 + 8 + 4;
+        const size_t per_q = size_t(X.d_pad) * 4 + size_t(X.qp_pad) * 6 + size_t(cfg.fes_T) * 4 + 8 + 4;
         char buf[400];
         snprintf(buf, sizeof buf,
                  "nq = %lld needs %zu bytes of scratch but pilot_search_noalloc holds %zu bytes (about %zu queries "
@@ -134,6 +135,7 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     io.q_pad = reinterpret_cast<float*>(base + o_qpad);
     io.qp = reinterpret_cast<float*>(base + o_qp);
     io.fes_pos = reinterpret_cast<int32_t*>(base + o_pos);
+    io.qp_bf16 = reinterpret_cast<uint16_t*>(base + o_qpb);
     io.fes_lb = reinterpret_cast<double*>(base + o_lb);
     io.bad_query = reinterpret_cast<int32_t*>(base + o_bad);
     io.out_ids = out_ids;
@@ -143,7 +145,7 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((e = cudaMemsetAsync(io.status, 0, 8 * 4, st)) != cudaSuccess) return cuda_error(e, "clear status");
     if ((e = launch_project(X, io, st)) != cudaSuccess) return cuda_error(e, "projection kernel");
-    if ((e = launch_fes_scores(X, cfg, io, st)) != cudaSuccess) return cuda_error(e, "FES scoring kernel");
+    if ((e = launch_fes_mma(X, io, st)) != cudaSuccess) return cuda_error(e, "FES tensor-core kernel");
     e = launch_search(X, cfg, io, st, v.num_sms);
     if (e == cudaErrorInvalidConfiguration) {
         cudaGetLastError();
@@ -154,6 +156,7 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
         return cuda_error(e, "read status");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
     if (v.status_host[2]) return error(PILOT_ETIMEOUT, "%lld search warps gave up waiting for a row gather", v.status_host[2]);
+    if (v.status_host[5]) return error(PILOT_ETIMEOUT, "%lld FES blocks gave up waiting for the tensor cores", v.status_host[5]);
     if (v.status_host[4]) return error(PILOT_ECUDA, "%lld queries hit the expansion cap", v.status_host[4]);
     if (v.status_host[0])
         return error(PILOT_EINVAL, "%lld queries hold NaN or infinity (their results are -1 / +inf)",

@@ -288,6 +288,17 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
         emax = std::max(emax, std::sqrt(nn));
     }
     X.entry_max_norm = float(emax * (1.0 + 1e-6));
+    // BF16 copy for the tensor-core FES scores: RNE of the decoded values,
+    // whole 256-row tiles (zero rows past n_entry) in the UMMA layout
+    const int64_t e_tiles = (D.n_entry + 255) / 256;
+    std::vector<uint16_t> entry_bf16(size_t(e_tiles * 256 * X.qp_pad), 0);
+    for (int64_t e = 0; e < D.n_entry; ++e)
+        for (int c = 0; c < X.qp_pad; ++c) {
+            uint32_t b;
+            std::memcpy(&b, &entry_f32[size_t(e * X.qp_pad + c)], 4);
+            const uint32_t r = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+            entry_bf16[size_t(umma_kmajor_offset(e, c, 256, X.qp_pad))] = uint16_t(r);
+        }
 
     if ((s = ix->upload(D.graph, size_t(n * D.R), &X.graph)) != PILOT_OK) return s;
     if ((s = ix->upload(sub_adj.data(), sub_adj.size(), &X.sub_adj)) != PILOT_OK) return s;
@@ -295,8 +306,9 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     if ((s = ix->upload(full2sub.data(), full2sub.size(), &X.full2sub)) != PILOT_OK) return s;
     if ((s = ix->upload(basis.data(), basis.size(), &X.basis)) != PILOT_OK) return s;
     if ((s = ix->upload(entry.data(), entry.size(), &X.entry)) != PILOT_OK) return s;
-    if ((s = ix->upload(entry_f32.data(), entry_f32.size(), &X.entry_f32)) != PILOT_OK) return s;
+    entry_n2.resize(size_t(e_tiles * 256), INFINITY);   // whole tiles; padded entries never score
     if ((s = ix->upload(entry_n2.data(), entry_n2.size(), &X.entry_norm2)) != PILOT_OK) return s;
+    if ((s = ix->upload(entry_bf16.data(), entry_bf16.size(), &X.entry_bf16)) != PILOT_OK) return s;
     X.red_scales = nullptr;
     if (D.reduced_dtype == 2)
         if ((s = ix->upload(D.reduced_scales, size_t(n_sub), &X.red_scales)) != PILOT_OK) return s;
@@ -474,6 +486,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     const size_t o_qpad = take(size_t(nq) * X.d_pad * 4);
     const size_t o_qp = take(size_t(nq) * X.qp_pad * 4);
     const size_t o_pos = take(size_t(nq) * cfg.fes_T * 4);
+    const size_t o_qpb = take(size_t((nq + 127) / 128 * 128) * X.qp_pad * 2);
     const size_t o_lb = take(size_t(nq) * 8);
     const size_t o_bad = take(size_t(nq) * 4);
     const size_t o_q = q_dev ? 0 : take(size_t(nq) * X.d * 4);
@@ -494,6 +507,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     io.q_pad = reinterpret_cast<float*>(ws + o_qpad);
     io.qp = reinterpret_cast<float*>(ws + o_qp);
     io.fes_pos = reinterpret_cast<int32_t*>(ws + o_pos);
+    io.qp_bf16 = reinterpret_cast<uint16_t*>(ws + o_qpb);
     io.fes_lb = reinterpret_cast<double*>(ws + o_lb);
     io.bad_query = reinterpret_cast<int32_t*>(ws + o_bad);
     io.queries = q_dev ? queries : reinterpret_cast<const float*>(ws + o_q);
@@ -511,7 +525,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[0], st));
     CUDA_TRY(launch_project(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[1], st));
-    if (cfg.use_fes) CUDA_TRY(launch_fes_scores(X, cfg, io, st));
+    if (cfg.use_fes) CUDA_TRY(launch_fes_mma(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[2], st));
     {
         cudaError_t e = launch_search(X, cfg, io, st, ix->num_sms);
@@ -533,7 +547,9 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (timed)
         for (int i = 0; i < 3; ++i) CUDA_TRY(cudaEventElapsedTime(&opt.kernel_ms[i], ix->ev[i], ix->ev[i + 1]));
     const int32_t* S = ix->status_host;
+    if (opt.status_words) std::memcpy(opt.status_words, S, 8 * sizeof(int32_t));
     if (S[2]) return fail(PILOT_ETIMEOUT, "%d search warps gave up waiting for a row gather", S[2]);
+    if (S[5]) return fail(PILOT_ETIMEOUT, "%d FES blocks gave up waiting for the tensor cores", S[5]);
     if (S[4]) return fail(PILOT_ECUDA, "%d queries hit the expansion cap", S[4]);
     if (S[0]) return fail(PILOT_EINVAL, "%d queries hold NaN or infinity (their results are -1 / +inf)", S[0]);
     return PILOT_OK;

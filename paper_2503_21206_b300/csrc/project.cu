@@ -5,6 +5,8 @@
 // FP32 rounding of the exact dot product with the FP64 basis column, which is
 // held as an exact-enough FP32 pair (hi, lo): sum_j q_j (hi_j + lo_j) is
 // accumulated with TwoProduct / TwoSum (device_common.cuh).
+#include <cuda_bf16.h>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(kWarps * 32) project_kernel(DevIndex ix, Searc
                 r = __fadd_rn(acc.hi, acc.lo);
             }
             io.qp[q * ix.qp_pad + c] = r;
+            if (io.qp_bf16) io.qp_bf16[umma_kmajor_offset(q, c, 128, ix.qp_pad)] = __bfloat16_as_ushort(__float2bfloat16_rn(r));
         }
         __syncwarp();
     }

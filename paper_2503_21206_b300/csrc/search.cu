@@ -941,7 +941,7 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.stage2_expansions = 2;
     cfg.stage3 = 1;
     cfg.use_fes = 1;
-    cfg.fes_T = 8;
+    cfg.fes_T = kFesT;
     cfg.warps_per_block = 2;
     int stage = 4 * (ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes);
     const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;

@@ -89,6 +89,7 @@ struct pilot_server {
     int32_t* next = nullptr;
     float *new_q = nullptr, *new_q_pad = nullptr, *new_qp = nullptr;
     int32_t *new_pos = nullptr, *new_bad = nullptr, *new_status = nullptr;
+    uint16_t* new_qpb = nullptr;
     double* new_lb = nullptr;
     // host-mapped
     ServeEntry* entries = nullptr;
@@ -211,12 +212,13 @@ pilot_status pilot_server::step() {
         io.q_pad = new_q_pad;
         io.qp = new_qp;
         io.fes_pos = new_pos;
+        io.qp_bf16 = new_qpb;
         io.fes_lb = new_lb;
         io.bad_query = new_bad;
         io.status = new_status;
         if ((e = launch_project(X, io, stream)) != cudaSuccess) return cuda_err(e, "projection kernel");
-        if (scfg.use_fes && (e = launch_fes_scores(X, scfg, io, stream)) != cudaSuccess)
-            return cuda_err(e, "FES scoring kernel");
+        if (scfg.use_fes && (e = launch_fes_mma(X, io, stream)) != cudaSuccess)
+            return cuda_err(e, "FES tensor-core kernel");
     }
     if ((e = cudaGraphLaunch(graph, stream)) != cudaSuccess) return cuda_err(e, "step graph");
     // bounded wait for the step
@@ -323,6 +325,7 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((ps = S->dalloc(&S->new_q_pad, size_t(NN) * X.d_pad)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_qp, size_t(NN) * X.qp_pad)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_pos, size_t(NN) * S->scfg.fes_T)) != PILOT_OK) return ps;
+    if ((ps = S->dalloc(&S->new_qpb, size_t((NN + 127) / 128 * 128) * X.qp_pad)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_lb, size_t(NN))) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_bad, size_t(NN))) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_status, 8)) != PILOT_OK) return ps;
