@@ -227,15 +227,20 @@ def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q:
 
 # ------------------------------------------------------------------ arms --
 
-def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, **cfg) -> dict:
+def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, fixed_ef: int = 0, **cfg) -> dict:
     """Poisson arrivals at `rate` requests/s of n_req requests with k drawn
-    from {1, 10, 100} and ef uniform in 32..512 (ef >= k), submitted from this
-    thread as their arrival times pass; returns the server's statistics and
+    from {1, 10, 100} and ef uniform in 32..512 (ef >= k) -- or, with
+    `fixed_ef`, k = 10 and that ef for all -- submitted from this thread as
+    their arrival times pass; returns the server's statistics and
     recall@min(k, 10) of the answers."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-    ks = rng.choice([1, 10, 100], size=n_req)
-    efs = np.array([int(rng.integers(max(32, k), 513)) for k in ks])
+    if fixed_ef:
+        ks = np.full(n_req, 10)
+        efs = np.full(n_req, fixed_ef)
+    else:
+        ks = rng.choice([1, 10, 100], size=n_req)
+        efs = np.array([int(rng.integers(max(32, k), 513)) for k in ks])
     rows = rng.integers(0, len(Q), n_req)
     srv = pilot.pilot_serve_create(g, **cfg)
     tickets = []
@@ -261,7 +266,8 @@ def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, **cfg) 
     return {"offered_rate": rate, "requests": n_req, "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
             "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3), "slots": st["slots"],
             "steps": st["steps"], "recall@min(k,10)": round(hits / tot, 5), "mean_ef": float(efs.mean()),
-            "k_mix": "1/10/100 uniform", "ef_mix": "uniform 32..512, ef >= k"}
+            "k_mix": "10" if fixed_ef else "1/10/100 uniform",
+            "ef_mix": f"{fixed_ef} for all" if fixed_ef else "uniform 32..512, ef >= k"}
 
 
 def run_reference(args):
@@ -308,6 +314,129 @@ def run_reference(args):
     return 0
 
 
+def distance_error(idx, Q, ids, dists) -> float:
+    """Largest relative error of the returned distances against the FP64
+    distances of the same ids (the FP64 brute-force definition)."""
+    worst = 0.0
+    for s in range(0, len(Q), 1024):
+        I = ids[s:s + 1024].astype(np.int64)
+        ok = I >= 0
+        X = idx.full[np.where(ok, I, 0)].astype(np.float64)
+        q = Q[s:s + 1024, None, :].astype(np.float64)
+        ref = ((X - q) ** 2).sum(-1) if idx.metric == 0 else -(X * q).sum(-1)
+        err = np.abs(dists[s:s + 1024].astype(np.float64) - ref) / np.maximum(np.abs(ref), 1e-30)
+        worst = max(worst, float(err[ok].max()) if ok.any() else 0.0)
+    return worst
+
+
+def timed_steps(search, stream, flush, steps: int, warmup: int, kms):
+    """(mean step ms, mean search-kernel ms) over `steps` device-timed calls,
+    L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        search()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    step_ms, search_ms = [], []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        ev0.record(stream)
+        search()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        search_ms.append(float(kms[2]))
+    return statistics.mean(step_ms), statistics.mean(search_ms)
+
+
+def run_forms(args):
+    """Precision forms of one workload on one GPU: reduced rows in FP32, BF16
+    and FP8-E4M3 (the workload's list), plus the plain form (only the final
+    stage: Algorithm 1 on the full graph with full rows, seeded by FES).  For
+    each, the smallest swept ef reaching recall@10 >= 0.95 against the FP64
+    brute force, batch QPS there, the search kernel's fraction of HBM peak, the
+    distance error against FP64, and a saturating serving run at that ef."""
+    import torch
+    from paper_2503_21206_b300 import pilot
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    w, idx32, Q, gt = load_workload(args.workload, args.n, args.nq)
+    if idx32.reduced_dtype != "f32":
+        raise SystemExit("--forms needs a workload whose index stores FP32 reduced rows")
+    red32 = idx32.reduced
+    nq, k = len(Q), w.k
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    cnt = torch.empty((nq, 8), dtype=torch.int32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    kms = np.zeros(3, np.float32)
+    peak, peak_kind = measured_peaks()
+    efs = [args.ef] if args.ef else list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
+    forms = [(dt, dict()) for dt in w.reduced_dtypes] + [("f32", dict(stage1=0, stage2_expansions=0))]
+    out = []
+    for dt, sw in forms:
+        idx = idx32 if dt == "f32" else idx32.with_reduced(dt, red32)
+        g = pilot.load_index_data(idx)
+        opts = pilot.pilot_search_options_default()
+        for key, v in sw.items():
+            setattr(opts, key, v)
+
+        def search(ef, counters=None):
+            return pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=opts, counters=counters,
+                                         kernel_ms=kms)
+
+        sweep, ef = [], None
+        for cand in efs:
+            search(cand)
+            torch.cuda.synchronize()
+            rec = recall_at_k(ids.cpu().numpy(), gt, k)
+            sweep.append({"ef": cand, "recall@10": round(rec, 5), "search_ms": round(float(kms[2]), 3)})
+            ef = cand
+            if rec >= 0.95:
+                break
+        tuned = None if args.no_autotune else pilot.pilot_autotune(g, qd, k, ef, stream, options=opts)
+        search(ef, cnt)
+        torch.cuda.synchronize()
+        counters = cnt.cpu().numpy()
+        h_ids, h_d = ids.cpu().numpy(), dists.cpu().numpy()
+        recall = recall_at_k(h_ids, gt, k)
+        step_ms, search_ms = timed_steps(lambda: search(ef), stream, flush, args.steps, args.warmup, kms)
+        alg = algorithmic_bytes(counters, k, idx)
+        c = counters.astype(np.float64)
+        rec_form = {"form": "plain (final stage only)" if sw else "staged", "reduced_dtype": dt, "ef": ef,
+                    "recall@10": round(recall, 5), "qps": nq / (step_ms / 1000.0), "ms_per_batch": step_ms,
+                    "search_kernel_ms": search_ms, "hbm_gbs": alg / (search_ms / 1000.0) / 1e9,
+                    "hbm_frac": alg / (search_ms / 1000.0) / 1e9 / peak,
+                    "max_rel_dist_err_vs_fp64": distance_error(idx, Q, h_ids, h_d), "sweep": sweep,
+                    "autotuned": tuned,
+                    "mean_counters": {name: round(float(c[:, i].mean()), 1) for i, name in
+                                      enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}}
+        if not args.no_serving and not sw:   # the server always runs every stage
+            rate = 2.0 * rec_form["qps"]
+            rec_form["serving"] = serving_run(pilot, g, Q, gt, rate, min(args.serve_requests, int(rate * 4) + 1000),
+                                              fixed_ef=ef, max_ef=512, max_k=100,
+                                              expansions_per_step=args.serve_budget)
+        out.append(rec_form)
+        print(json.dumps(rec_form), file=sys.stderr, flush=True)
+        g.free()
+        del g
+    base = next(f for f in out if f["form"] != "staged")
+    line = {"metric": "QPS@recall10=0.95 by precision form", "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": args.workload, "n": idx32.n, "d": idx32.d, "dp": idx32.dp, "nq": nq, "k": k,
+                       "metric": "ip" if idx32.metric else "l2", "R": int(idx32.graph.shape[1]),
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
+            "peak": {"hbm_gbs": peak, "source": peak_kind},
+            "forms": out,
+            "qps_vs_plain": {f["reduced_dtype"] + ("" if f["form"] == "staged" else "_plain"):
+                             round(f["qps"] / base["qps"], 3) for f in out}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_pilot(args):
     import torch
     ws, rank, local = dist_env()
@@ -348,6 +477,12 @@ def run_pilot(args):
         ef = cand
         if rec >= 0.95:
             break
+    # the library's autotuner picks the launch shape for this ef on the batch
+    # itself (it leaves results unchanged; explicit --warps-per-block /
+    # --stage-rows still override it)
+    tuned = None
+    if not args.no_autotune:
+        tuned = pilot.pilot_autotune(g, qd, k, ef, stream, options=opts)
     search(qd, ef, ids, dists, cnt)
     torch.cuda.synchronize()
     counters = cnt.cpu().numpy()
@@ -396,6 +531,21 @@ def run_pilot(args):
     e2e_value = aggregate_throughput(nq * len(e2e_s), ws, reduce_max(sum(e2e_s), device))
     e2e_recall = recall_at_k(ids_h.numpy(), gt, k)
 
+    # ---- per-stage split: stage (1) + re-rank alone (stages (2)(3) off), the
+    # rest by difference; algorithmic bytes from each run's own counters
+    o1 = pilot.pilot_search_options_default()
+    for key in ("warps_per_block", "stage_rows"):
+        setattr(o1, key, getattr(opts, key))
+    o1.stage2_expansions, o1.stage3 = 0, 0
+    cnt1 = torch.empty_like(cnt)
+    pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=o1, counters=cnt1, kernel_ms=kms)
+    torch.cuda.synchronize()
+    c1 = cnt1.cpu().numpy()
+    _, s1_ms = timed_steps(lambda: pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=o1,
+                                                         kernel_ms=kms), stream, flush, args.steps, 3, kms)
+    s1_bytes = algorithmic_bytes(c1, k, idx)
+    stage_split = {"stage1_rerank_ms": s1_ms, "stage1_rerank_gbs": s1_bytes / (s1_ms / 1000.0) / 1e9,
+                   "stage23_ms_by_difference": None, "stage23_gbs_by_difference": None}
     serving = None
     if not args.no_serving:
         serving = serving_run(pilot, g, Q, gt, args.serve_rate, args.serve_requests, max_ef=512, max_k=100,
@@ -403,6 +553,10 @@ def run_pilot(args):
     peak, peak_kind = measured_peaks()
     mean_search_ms = statistics.mean(search_ms)
     achieved = alg_bytes / (mean_search_ms / 1000.0) / 1e9
+    if mean_search_ms > s1_ms:
+        stage_split["stage23_ms_by_difference"] = mean_search_ms - s1_ms
+        stage_split["stage23_gbs_by_difference"] = (alg_bytes - s1_bytes) / ((mean_search_ms - s1_ms) / 1000.0) / 1e9
+    stage_split["stage1_rerank_frac"] = stage_split["stage1_rerank_gbs"] / peak
     if rank != 0:
         return 0
     cpu = None
@@ -419,7 +573,7 @@ def run_pilot(args):
                    "recall@10": round(recall, 5), "R": int(idx.graph.shape[1]), "sample_ratio": w.sample_ratio,
                    "n_entry": int(len(idx.entry_ids)), "reduced_dtype": idx.reduced_dtype,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "sweep": sweep,
-                   "parallelism": f"replicas x{ws}",
+                   "parallelism": f"replicas x{ws}", "autotuned": tuned,
                    "mean_counters": {name: round(float(c[:, i].mean()), 2) for i, name in
                                      enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(nq * idx.d * 4),
@@ -430,6 +584,7 @@ def run_pilot(args):
                      "peak_source": f"{peak_kind} hbm_gbs (copy)", "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_kernel_ms": mean_search_ms},
         "kernel_ms": {"project": float(kms[0]), "fes_scores": float(kms[1]), "search": mean_search_ms},
+        "stage_split": stage_split,
         "clocks": clocks, "wall_s_timed": round(t_wall, 4),
     }
     if cpu is not None:
@@ -457,10 +612,15 @@ def main(argv=None):
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-budget", type=int, default=128, help="expansions per request per step")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--forms", action="store_true",
+                    help="compare the reduced-row precision forms and the plain form (one GPU)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    return run_reference(args) if args.impl == "reference" else run_pilot(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_forms(args) if args.forms else run_pilot(args)
 
 
 if __name__ == "__main__":

@@ -127,8 +127,10 @@ typedef struct {
     int32_t stage2_expansions;  /* stage (2) subgraph expansions (default 2, Sec. 4.1 (2)) */
     int32_t stage3;             /* 1: run stage (3) (default 1) */
     int32_t use_fes;            /* 1: FES entry (default); 0: entry_ids[0] */
-    int32_t warps_per_block;    /* search warps (one query each) per block, 1..8; 0 = automatic */
-    int32_t stage_rows;         /* rows gathered per pass into shared memory, 4..32; 0 = automatic */
+    int32_t warps_per_block;    /* search warps (one query each) per block, 1..8; 0 = automatic
+                                   (the autotuned shape of the ef class, else 2) */
+    int32_t stage_rows;         /* rows of the widest kind gathered per pass into shared memory, 4..32
+                                   (clamped; a multiple of 4); 0 = automatic (autotuned or default) */
     int32_t* counters;          /* optional nq x 8 int32 (host or device): per query the
                                    expansions and distances of stages (1), (2), (3), the
                                    number of re-ranked candidates and the entry id */
@@ -229,6 +231,49 @@ pilot_status pilot_serve_wait(pilot_server* server, uint64_t ticket, int timeout
 pilot_status pilot_serve_stats(pilot_server* server, pilot_serve_statistics* stats);
 /* Stop the background thread and free the server (pending tickets are lost). */
 void pilot_serve_destroy(pilot_server* server);
+
+/*
+ * Autotuner: picks the search kernel's launch shape for one index and one
+ * class of ef (the candidate list's power-of-two capacity: ef in 1..32,
+ * 33..64, ..., 257..512).  The paper has no counterpart; it tunes only how
+ * the same search is laid out on the GPU, so results do not change.
+ *
+ * Times the search kernel (CUDA events, 1 untimed + 3 timed runs each, the
+ * median kept) on the caller's `queries` (nq x d float32, host or device) at
+ * (k, ef), with the stage switches of `base` (stage1, stage2_expansions,
+ * stage3, use_fes; NULL = the defaults; its other fields are ignored), for
+ * every pair of
+ *   warps_per_block  in {1, 2, 4, 8}   (queries per block; one warp each)
+ *   stage_rows       in {4, 8, 16, 32} (rows staged per gather pass)
+ * whose shared memory fits, and for the defaults.  The fastest becomes the
+ * index's shape for that ef class: pilot_search / pilot_search_ex calls whose
+ * options leave warps_per_block or stage_rows at 0, and servers created on
+ * the index afterwards whose max_ef falls in that class, use it.
+ * (pilot_search_noalloc keeps the defaults.)
+ *
+ * cache_path (may be NULL): a text file of lines
+ *   "<key> <warps_per_block> <stage_rows> <best_ms>"
+ * where key names the device model, the index shape (n, d, d', reduced
+ * type, metric, R, R_sub, n_sub, entries), the ef class and the stage
+ * switches.  A class holds one shape: the last tuning of it wins.  When the file
+ * holds the key, its shape is applied without timing (from_cache = 1);
+ * otherwise the timed result is appended.  An unreadable file counts as
+ * empty; a write failure is ignored (the tuned shape still applies).
+ * Errors: PILOT_EINVAL for the arguments pilot_search rejects, nq < 1 or a
+ * NULL index / queries; search errors are passed on.  Not thread-safe with
+ * other calls on the same index that rely on automatic shapes.
+ */
+typedef struct {
+    int32_t warps_per_block;   /* chosen shape */
+    int32_t stage_rows;
+    int32_t candidates;        /* shapes timed (0 when read from the cache) */
+    int32_t from_cache;        /* 1 when the shape came from cache_path */
+    float best_ms;             /* median search-kernel time of the chosen shape */
+    float default_ms;          /* the same for the default shape (0 from the cache) */
+} pilot_tune_result;
+
+pilot_status pilot_autotune(pilot_index* index, const float* queries, int64_t nq, int k, int ef, void* stream,
+                            const pilot_search_options* base, const char* cache_path, pilot_tune_result* result);
 
 /* The calling thread's last error message ("" if none). */
 const char* pilot_last_error(void);

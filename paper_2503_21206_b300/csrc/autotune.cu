@@ -1,0 +1,187 @@
+// autotune.cu -- the project's autotuner for the search kernel's launch shape
+// (queries per block and rows staged per gather pass), with a text cache.
+// It times whole pilot_search_ex calls through the public entry point and
+// reads the search kernel's own event time, so what it measures is what a
+// caller runs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/pilot.h"
+#include "kernels.h"
+
+namespace pilot {
+IndexView index_view(pilot_index* ix);
+int set_error(int status, const char* msg);
+}  // namespace pilot
+
+using namespace pilot;
+
+namespace {
+
+pilot_status tune_fail(pilot_status s, const std::string& msg) { return pilot_status(set_error(int(s), msg.c_str())); }
+
+std::string tune_key(const DevIndex& X, int device, int cls) {
+    cudaDeviceProp p{};
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&p, device) == cudaSuccess) name = p.name;
+    else cudaGetLastError();
+    for (char& c : name)
+        if (c == ' ' || c == '\t') c = '_';
+    std::ostringstream o;
+    o << name << "|n" << X.n << "|d" << X.d << "|dp" << X.dp << "|t" << X.red_dtype << "|m" << X.metric << "|R"
+      << X.R << "|Rs" << X.R_sub << "|ns" << X.n_sub << "|e" << X.n_entry << "|ef" << (1 << cls);
+    return o.str();
+}
+
+// The last line of `path` whose key matches; false when none (or unreadable).
+bool cache_lookup(const char* path, const std::string& key, TunedShape* out) {
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        std::string k;
+        int w = 0, r = 0;
+        if (!(in >> k >> w >> r) || k != key || w < 1 || w > 8 || (r != 0 && (r < 4 || r > 32))) continue;
+        out->warps_per_block = w;
+        out->stage_rows = r;
+        found = true;
+    }
+    return found;
+}
+
+struct Timed {
+    int wpb, rows;
+    float ms;
+};
+
+}  // namespace
+
+extern "C" pilot_status pilot_autotune(pilot_index* index, const float* queries, int64_t nq, int k, int ef,
+                                       void* stream, const pilot_search_options* base, const char* cache_path,
+                                       pilot_tune_result* result) {
+    if (!index) return tune_fail(PILOT_EINVAL, "index is NULL");
+    if (!queries || nq < 1) return tune_fail(PILOT_EINVAL, "autotuning needs at least one query");
+    if (k < 1 || ef < k || ef > PILOT_MAX_EF) return tune_fail(PILOT_EINVAL, "k / ef outside the search limits");
+    const IndexView v = index_view(index);
+    std::mutex& mu = *static_cast<std::mutex*>(v.mutex);
+    const int cls = ef_class(ef);
+    pilot_search_options stages;
+    pilot_search_options_default(&stages);
+    if (base) {   // only the stage switches are taken from the caller
+        stages.stage1 = base->stage1;
+        stages.stage2_expansions = base->stage2_expansions;
+        stages.stage3 = base->stage3;
+        stages.use_fes = base->use_fes;
+    }
+    const std::string key = tune_key(*v.dev, v.device, cls) + "|s" + std::to_string(stages.stage1 != 0) + "." +
+                            std::to_string(stages.stage2_expansions) + "." + std::to_string(stages.stage3 != 0) +
+                            "." + std::to_string(stages.use_fes != 0);
+    pilot_tune_result res{};
+
+    if (cache_path) {
+        TunedShape t{};
+        if (cache_lookup(cache_path, key, &t)) {
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                v.tuned[cls] = t;
+            }
+            res.warps_per_block = t.warps_per_block;
+            res.stage_rows = t.stage_rows;
+            res.from_cache = 1;
+            if (result) *result = res;
+            return PILOT_OK;
+        }
+    }
+
+    cudaError_t e = cudaSetDevice(v.device);
+    if (e != cudaSuccess) return tune_fail(PILOT_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    int32_t* ids = nullptr;
+    float* dists = nullptr;
+    if ((e = cudaMalloc(&ids, size_t(nq) * k * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&dists, size_t(nq) * k * 4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ids);
+        return tune_fail(PILOT_ENOMEM, "autotune output buffers");
+    }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        v.tuned[cls] = TunedShape{};   // time the defaults as they are
+    }
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, v.device);
+    pilot_status ps = PILOT_OK;
+    // median search-kernel time of one shape; -1 when its shared memory does not fit
+    auto time_shape = [&](int wpb, int rows, float* ms_out) -> pilot_status {
+        SearchConfig cfg = default_search_config(*v.dev, k, ef);
+        if (wpb > 0) cfg.warps_per_block = wpb;
+        if (rows > 0) set_stage_rows(*v.dev, cfg, rows);
+        if (search_smem_per_warp(*v.dev, cfg) * size_t(cfg.warps_per_block) > size_t(smem_max)) {
+            *ms_out = -1.0f;
+            return PILOT_OK;
+        }
+        pilot_search_options o = stages;
+        o.warps_per_block = wpb;
+        o.stage_rows = rows;
+        float kms[3] = {0, 0, 0};
+        o.kernel_ms = kms;
+        std::vector<float> t;
+        for (int rep = 0; rep < 4; ++rep) {
+            pilot_status s = pilot_search_ex(index, queries, nq, k, ef, ids, dists, stream, &o);
+            if (s != PILOT_OK) return s;
+            if (rep > 0) t.push_back(kms[2]);
+        }
+        std::sort(t.begin(), t.end());
+        *ms_out = t[t.size() / 2];
+        return PILOT_OK;
+    };
+    float def_ms = 0.0f;
+    ps = time_shape(0, 0, &def_ms);
+    std::vector<Timed> timed;
+    if (ps == PILOT_OK && def_ms < 0.0f) ps = tune_fail(PILOT_EINVAL, "the default shape does not fit this ef");
+    for (int wpb : {1, 2, 4, 8}) {
+        for (int rows : {4, 8, 16, 32}) {
+            if (ps != PILOT_OK) break;
+            float ms = 0.0f;
+            ps = time_shape(wpb, rows, &ms);
+            if (ps == PILOT_OK && ms >= 0.0f) timed.push_back({wpb, rows, ms});
+        }
+    }
+    cudaFree(ids);
+    cudaFree(dists);
+    if (ps != PILOT_OK) return ps;
+
+    res.candidates = int(timed.size());
+    res.default_ms = def_ms;
+    res.best_ms = def_ms;
+    TunedShape best{};   // the defaults unless a timed shape beats them
+    for (const Timed& t : timed)
+        if (t.ms < res.best_ms) {
+            res.best_ms = t.ms;
+            best = TunedShape{t.wpb, t.rows};
+        }
+    if (best.warps_per_block == 0) {   // record the defaults explicitly, as the shape they resolve to
+        best.warps_per_block = 2;
+        best.stage_rows = 0;
+    }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        v.tuned[cls] = best;
+    }
+    res.warps_per_block = best.warps_per_block;
+    res.stage_rows = best.stage_rows;
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        if (f) f << key << ' ' << best.warps_per_block << ' ' << best.stage_rows << ' ' << res.best_ms << '\n';
+    }
+    if (result) *result = res;
+    return PILOT_OK;
+}

@@ -10,6 +10,9 @@
 // exact value lies within ~2^-40 (relative) of an FP32 rounding boundary.
 #pragma once
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include <cstdint>
 
 namespace pilot {
@@ -119,6 +122,17 @@ __device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
     uint32_t m = c & 7u;
     if (e == 0) return __uint_as_float(s | __float_as_uint(__uint2float_rn(m) * 0.001953125f));
     return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
+}
+
+// Four E4M3 codes (one 32-bit word, first code in the low byte) -> FP32,
+// exactly, through the hardware pair conversion to FP16 (E4M3 is a subset).
+__device__ __forceinline__ void e4m3x4_to_f32(uint32_t wv, float (&x)[4]) {
+    const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(wv & 0xFFFFu), __NV_E4M3);
+    const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(wv >> 16), __NV_E4M3);
+    x[0] = __half2float(__ushort_as_half(a.x));
+    x[1] = __half2float(__ushort_as_half(a.y));
+    x[2] = __half2float(__ushort_as_half(b.x));
+    x[3] = __half2float(__ushort_as_half(b.y));
 }
 
 // ------------------------------------------------------------------ keys --

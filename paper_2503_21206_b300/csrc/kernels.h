@@ -134,12 +134,26 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef);
 void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows);
 
 // Internal view of a loaded index for entry points outside pilot_api.cu.
+// Search shape chosen by the autotuner for one class of ef: the candidate
+// list's power-of-two capacity 2^c, c = 5..9.  Zeros keep the defaults.
+struct TunedShape {
+    int warps_per_block;
+    int stage_rows;
+};
+constexpr int kEfClasses = 10;
+inline int ef_class(int ef) {
+    int c = 5;
+    while (c < kEfClasses - 1 && (1 << c) < ef) ++c;
+    return c;
+}
+
 struct IndexView {
     const DevIndex* dev;
     int device;
     int num_sms;
     int32_t* status_host;   // pinned, 8 words
     void* mutex;            // std::mutex guarding per-index state
+    TunedShape* tuned;      // kEfClasses entries, guarded by `mutex`
 };
 int search_blocks_per_sm(const DevIndex& ix, const SearchConfig& cfg);
 

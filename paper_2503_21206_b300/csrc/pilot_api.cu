@@ -71,6 +71,7 @@ struct pilot_index {
     int32_t* status_host = nullptr;   // pinned
     size_t device_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // per-kernel timing (on request)
+    TunedShape tuned[kEfClasses] = {};   // autotuned search shapes by ef class
 
     ~pilot_index() {
         for (cudaEvent_t e : ev)
@@ -113,7 +114,7 @@ namespace pilot {
 
 // Internal helpers for entry points defined in other translation units.
 IndexView index_view(pilot_index* ix) {
-    return IndexView{&ix->dev, ix->device, ix->num_sms, ix->status_host, &ix->mu};
+    return IndexView{&ix->dev, ix->device, ix->num_sms, ix->status_host, &ix->mu, ix->tuned};
 }
 
 int set_error(int status, const char* msg) {
@@ -468,8 +469,12 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cfg.stage2_expansions = opt.stage2_expansions;
     cfg.stage3 = opt.stage3 != 0;
     cfg.use_fes = opt.use_fes != 0;
-    if (opt.warps_per_block > 0) cfg.warps_per_block = std::min(opt.warps_per_block, 8);
-    if (opt.stage_rows > 0) set_stage_rows(X, cfg, opt.stage_rows);
+    // explicit options first, then the autotuned shape of this ef class, then the defaults
+    const TunedShape& tuned = ix->tuned[ef_class(ef)];
+    const int wpb = opt.warps_per_block > 0 ? opt.warps_per_block : tuned.warps_per_block;
+    const int rows = opt.stage_rows > 0 ? opt.stage_rows : tuned.stage_rows;
+    if (wpb > 0) cfg.warps_per_block = std::min(wpb, 8);
+    if (rows > 0) set_stage_rows(X, cfg, rows);
 
     const bool q_dev = is_device_ptr(queries);
     const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);

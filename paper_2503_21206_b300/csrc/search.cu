@@ -121,12 +121,17 @@ __device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, f
         for (int h = 0; h < 4; ++h) {
             const float4 qv = *reinterpret_cast<const float4*>(qc + h * 4);
             const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+            float c[4];
+            e4m3x4_to_f32(wv[h], c);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                float xl;
-                const float xh = two_prod(e4m3_to_f32((wv[h] >> (8 * b)) & 0xFFu), sc, xl);
-                if (METRIC == 0) l2_acc2(acc, qa[b], xh, xl);
-                else ip_acc2(acc, qa[b], xh, xl);
+                if (METRIC == 0) {
+                    float xl;
+                    const float xh = two_prod(c[b], sc, xl);   // code * scale = xh + xl exactly
+                    l2_acc2(acc, qa[b], xh, xl);
+                } else {
+                    ip_acc(acc, qa[b], c[b]);   // sum q * code; the row's scale is applied once at the end
+                }
             }
         }
     }
@@ -147,8 +152,10 @@ __device__ __forceinline__ void approx_chunk(float& a, float& b, uint4 v, const 
             x[0] = bf16_to_f32(wv[h] & 0xFFFFu);
             x[PER - 1] = bf16_to_f32(wv[h] >> 16);
         } else {
+            float c[4];
+            e4m3x4_to_f32(wv[h], c);
 #pragma unroll
-            for (int e = 0; e < PER; ++e) x[e] = e4m3_to_f32((wv[h] >> (8 * e)) & 0xFFu) * sc;
+            for (int e = 0; e < PER; ++e) x[e] = c[e] * sc;
         }
         if (DT == 0) {
             qe[0] = qc[h];
@@ -241,8 +248,15 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
             }
         }
     }
-    const DF sum = reduce8(acc, mm);
+    DF sum = reduce8(acc, mm);
     const int i = g + 4 * mm;
+    if (DT == 2 && METRIC == 1) {
+        // sum q_e (c_e s) = s * sum q_e c_e exactly; scale the pair once
+        const float s = i < m ? __ldg(scales + w.cand[cand_off + sel(i)]) : 1.0f;
+        float e;
+        const float p = two_prod(sum.hi, s, e);
+        sum = DF{p, __fmaf_rn(sum.lo, s, e)};
+    }
     if (i < m) w.dist[cand_off + sel(i)] = df_finish(sum, METRIC);
 }
 

@@ -296,6 +296,12 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
 
     // shared-memory budget: the step kernel's per-block slice for max_ef
     S->scfg = default_search_config(X, c.max_k, c.max_ef);
+    {   // the autotuned shape of max_ef's class, if the index has one
+        std::lock_guard<std::mutex> lock(*static_cast<std::mutex*>(S->view.mutex));
+        const TunedShape t = S->view.tuned[ef_class(int(c.max_ef))];
+        if (t.warps_per_block > 0) S->scfg.warps_per_block = std::min(t.warps_per_block, 8);
+        if (t.stage_rows > 0) set_stage_rows(X, S->scfg, t.stage_rows);
+    }
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->view.device);
     if (serve_smem_per_block(X, S->scfg) > size_t(smem_max))

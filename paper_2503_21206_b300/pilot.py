@@ -210,6 +210,35 @@ def pilot_search_noalloc(index: PilotIndex, queries, k: int, ef: int, out_ids, o
     return out_ids, out_dists
 
 
+# --------------------------------------------------------------- autotune --
+
+class pilot_tune_result(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("stage_rows", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float)]
+
+
+_lib.pilot_autotune.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P,
+                                ctypes.POINTER(pilot_search_options), ctypes.c_char_p,
+                                ctypes.POINTER(pilot_tune_result)]
+
+
+def pilot_autotune(index: PilotIndex, queries, k: int, ef: int, stream=None, *,
+                   options: pilot_search_options | None = None, cache_path: str | None = None) -> dict:
+    """Pick the search kernel's launch shape for ``index`` and ef's class by
+    timing the caller's queries with the stage switches of ``options`` (see
+    include/pilot.h); later searches with automatic options use it.  Returns
+    the result fields as a dict."""
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    r = pilot_tune_result()
+    _check(_lib.pilot_autotune(index.handle, _addr(queries), int(queries.shape[0]), k, ef, s,
+                               ctypes.byref(options) if options is not None else None,
+                               cache_path.encode() if cache_path else None, ctypes.byref(r)))
+    return {name: getattr(r, name) for name, _ in pilot_tune_result._fields_}
+
+
 # ---------------------------------------------------------------- serving --
 
 class pilot_serve_config(ctypes.Structure):

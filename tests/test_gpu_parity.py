@@ -221,6 +221,20 @@ def test_inner_product_metric(pilot, torch_cuda, dtype):
     assert np.array_equal(cnt, ref["counters"])
 
 
+@pytest.mark.parametrize("stage_rows", [4, 8, 12, 20])
+def test_wide_rows_multi_pass(pilot, torch_cuda, stage_rows):
+    """d = 768: a batch of up to 32 full rows (3 KB each) is gathered in
+    several passes through two half-buffers; every staging size gives the
+    oracle's results."""
+    w = synth.WORKLOADS["c3_powerlaw_2m_d768"]
+    idx, Q, red32, _ = index_build.build_workload(w, n=4000, nq=24, reduced_dtype="bf16")
+    g = pilot.load_index_data(idx)
+    ref = oracle.search(oracle_index(idx), Q, 10, 48)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 48, stage_rows=stage_rows)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
 def test_load_from_files(c1, pilot, torch_cuda, tmp_path):
     w, idx, Q, _, g = c1
     index_build.save_index(idx, str(tmp_path))
