@@ -611,7 +611,7 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) run")
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-requests", type=int, default=100_000)
-    ap.add_argument("--serve-budget", type=int, default=128, help="expansions per request per step")
+    ap.add_argument("--serve-budget", type=int, default=256, help="expansions per request per step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--forms", action="store_true",
                     help="compare the reduced-row precision forms and the plain form (one GPU)")

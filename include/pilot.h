@@ -190,8 +190,10 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  * at most expansions_per_step expansions of the staged search in one
  * persistent launch replayed from a CUDA graph; a request's candidate list,
  * visited bytes and phase stay in device memory between steps.  Requests
- * that arrive while others run join at the next step.  Each request's result
- * equals pilot_search's for the same query, k and ef.
+ * that arrive while others run join at a following step.  Steps are
+ * pipelined two deep: the next step is enqueued before the host completes
+ * the previous one.  Each request's result equals pilot_search's for the
+ * same query, k and ef.
  *
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
@@ -203,7 +205,7 @@ typedef struct {
     int32_t max_slots;            /* requests in flight at most (default 4096) */
     int32_t max_ef;               /* largest ef a request may use (default 512) */
     int32_t max_k;                /* largest k (default 100) */
-    int32_t expansions_per_step;  /* per request per step (default 64) */
+    int32_t expansions_per_step;  /* per request per step (default 256) */
     int32_t max_new_per_step;     /* admissions per step (default 1024) */
     int32_t step_timeout_ms;      /* a step longer than this fails the server (default 10000) */
     int64_t queue_capacity;       /* waiting requests before PILOT_EBUSY (default 2^20) */

@@ -785,8 +785,9 @@ __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig c
 // One serving step: every active request advances by at most sio.budget
 // expansions.  A request admitted in this step starts with FES (its
 // projection and FES scores were computed for the step's new rows); others
-// resume from their slot.  Finished requests write their top-k to the
-// host-mapped result rows and raise their done flag.
+// resume from their slot, and slots already finished are skipped.  Finished
+// requests write their top-k to the host-mapped result rows, mark their slot
+// done and raise their done flag.
 template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConfig cfg, ServeIO sio, Layout L) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -818,6 +819,9 @@ __global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConf
             k = e.k;
             s.fes(st, sio.new_fes_pos + int64_t(e.new_idx) * cfg.fes_T, sio.new_fes_lb[e.new_idx]);
         } else {
+            // a request that finished in the previous step is listed again
+            // when the host prepared this step before seeing it finish
+            if (ss->phase == kDone) continue;
             s.load_query(sq, sqp);
             st.phase = ss->phase; st.it = ss->it;
             st.e1 = ss->e1; st.d1 = ss->d1; st.e2 = ss->e2; st.d2 = ss->d2; st.e3 = ss->e3; st.d3 = ss->d3;
@@ -839,6 +843,7 @@ __global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConf
             __threadfence_system();
             if (w.lane == 0) {
                 ss->epoch_ctr = w.epoch_ctr;
+                ss->phase = kDone;
                 sio.res_done[e.slot] = w.failed ? 2 : 1;
             }
         } else {

@@ -7,9 +7,15 @@
 // request advances by at most `expansions_per_step` expansions of the staged
 // search, keeping its candidate list, visited bytes and phase in device
 // memory between steps.  Requests that arrive while others are on the GPU
-// join at the next step, so their work overlaps.  Finished requests write
+// join at a following step, so their work overlaps.  Finished requests write
 // their top-k to host-mapped memory; the thread completes their tickets and
 // records submit-to-completion latency.
+//
+// Steps are pipelined two deep: the thread prepares and enqueues step N+1
+// (its own host-mapped entry list, staging rows and captured graph) before it
+// waits for step N and completes N's requests, so the GPU does not idle
+// while the host works.  Step N+1 may list requests that finish in step N;
+// the step kernel skips slots whose state is already done.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,15 +97,17 @@ struct pilot_server {
     int32_t *new_pos = nullptr, *new_bad = nullptr, *new_status = nullptr;
     uint16_t* new_qpb = nullptr;
     double* new_lb = nullptr;
-    // host-mapped
-    ServeEntry* entries = nullptr;
-    int32_t* n_active = nullptr;
+    // host-mapped; entry lists, counts and staging rows per step parity
+    ServeEntry* entries[2] = {nullptr, nullptr};
+    int32_t* n_active[2] = {nullptr, nullptr};
     int32_t *res_ids = nullptr, *res_done = nullptr, *res_counters = nullptr;
     float* res_dists = nullptr;
-    float* staging_q = nullptr;   // pinned, new requests' vectors
+    float* staging_q[2] = {nullptr, nullptr};   // pinned, new requests' vectors
 
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaEvent_t step_done[2] = {nullptr, nullptr};
+    bool in_flight[2] = {false, false};
 
     // host state
     std::thread worker;
@@ -139,71 +147,90 @@ struct pilot_server {
     }
 
     ~pilot_server() {
-        if (graph) cudaGraphExecDestroy(graph);
+        if (stream) cudaStreamSynchronize(stream);
+        for (int p = 0; p < 2; ++p) {
+            if (graph[p]) cudaGraphExecDestroy(graph[p]);
+            if (step_done[p]) cudaEventDestroy(step_done[p]);
+        }
         if (stream) cudaStreamDestroy(stream);
         for (void* p : dev_allocs) cudaFree(p);
         for (void* p : host_allocs) cudaFreeHost(p);
     }
 
     void loop();
-    pilot_status step();
+    pilot_status enqueue(int p, bool* launched);
+    pilot_status complete(int p);
 };
 
 void pilot_server::loop() {
     cudaSetDevice(view.device);
+    int p = 0;   // parity of the next step to enqueue
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return stop || !queue.empty() || !active.empty(); });
+            const bool busy = in_flight[0] || in_flight[1];
+            if (!busy)
+                cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                                 [&] { return stop || !queue.empty() || !active.empty(); });
             if (stop) return;
-            if (queue.empty() && active.empty()) continue;
             if (broken != PILOT_OK) {   // fail everything still pending
                 for (Request& r : queue) results[r.ticket] = Result{broken, {}, {}};
                 queue.clear();
                 cv_done.notify_all();
                 continue;
             }
+            if (!busy && queue.empty() && active.empty()) continue;
         }
-        pilot_status s = step();
+        bool launched = false;
+        pilot_status s = enqueue(p, &launched);
+        if (s == PILOT_OK && in_flight[p ^ 1]) s = complete(p ^ 1);
         if (s != PILOT_OK) {
+            if (stream) cudaStreamSynchronize(stream);
+            in_flight[0] = in_flight[1] = false;
             std::lock_guard<std::mutex> lk(mu);
             broken = s;
             for (int slot : active) results[slot_req[size_t(slot)].ticket] = Result{s, {}, {}};
             active.clear();
             cv_done.notify_all();
+            continue;
         }
+        if (launched) p ^= 1;
     }
 }
 
-// One step: admit, project + score new requests, advance every request,
-// complete the finished ones.
-pilot_status pilot_server::step() {
+// Prepare and enqueue a step on parity p: admit queued requests into free
+// slots, list every occupied slot, upload, project and score the new ones,
+// and launch the step graph.  Nothing is launched when no slot is occupied.
+pilot_status pilot_server::enqueue(int p, bool* launched) {
+    *launched = false;
     int n_new = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
         int n = 0;
         const int cap_new = std::min<int>(int(free_slots.size()), cfg.max_new_per_step);
+        ServeEntry* E = entries[p];
         while (!queue.empty() && n_new < cap_new) {
             Request r = std::move(queue.front());
             queue.pop_front();
             const int slot = free_slots.back();
             free_slots.pop_back();
-            std::memcpy(staging_q + size_t(n_new) * size_t(X.d), r.q.data(), size_t(X.d) * 4);
-            res_done[slot] = 0;
-            entries[n++] = ServeEntry{slot, n_new, r.k, r.ef};
+            std::memcpy(staging_q[p] + size_t(n_new) * size_t(X.d), r.q.data(), size_t(X.d) * 4);
+            reinterpret_cast<volatile int32_t*>(res_done)[slot] = 0;
+            E[n++] = ServeEntry{slot, n_new, r.k, r.ef};
             r.q.clear();
             slot_req[size_t(slot)] = std::move(r);
             ++n_new;
             ++admitted;
         }
-        for (int slot : active) entries[n++] = ServeEntry{slot, -1, slot_req[size_t(slot)].k, slot_req[size_t(slot)].ef};
-        for (int i = 0; i < n_new; ++i) active.push_back(entries[i].slot);
-        *n_active = n;
+        for (int slot : active) E[n++] = ServeEntry{slot, -1, slot_req[size_t(slot)].k, slot_req[size_t(slot)].ef};
+        for (int i = 0; i < n_new; ++i) active.push_back(E[i].slot);
+        *reinterpret_cast<volatile int32_t*>(n_active[p]) = n;
+        if (n == 0) return PILOT_OK;
     }
     cudaError_t e;
     if (n_new > 0) {
-        if ((e = cudaMemcpyAsync(new_q, staging_q, size_t(n_new) * size_t(X.d) * 4, cudaMemcpyHostToDevice, stream)) !=
-            cudaSuccess)
+        if ((e = cudaMemcpyAsync(new_q, staging_q[p], size_t(n_new) * size_t(X.d) * 4, cudaMemcpyHostToDevice,
+                                 stream)) != cudaSuccess)
             return cuda_err(e, "copy new requests");
         if ((e = cudaMemsetAsync(new_status, 0, 8 * 4, stream)) != cudaSuccess) return cuda_err(e, "clear status");
         SearchIO io{};
@@ -220,17 +247,26 @@ pilot_status pilot_server::step() {
         if (scfg.use_fes && (e = launch_fes_mma(X, io, stream)) != cudaSuccess)
             return cuda_err(e, "FES tensor-core kernel");
     }
-    if ((e = cudaGraphLaunch(graph, stream)) != cudaSuccess) return cuda_err(e, "step graph");
-    // bounded wait for the step
+    if ((e = cudaGraphLaunch(graph[p], stream)) != cudaSuccess) return cuda_err(e, "step graph");
+    if ((e = cudaEventRecord(step_done[p], stream)) != cudaSuccess) return cuda_err(e, "record step");
+    in_flight[p] = true;
+    *launched = true;
+    return PILOT_OK;
+}
+
+// Wait (bounded) for the step on parity p, then complete every occupied slot
+// whose done flag is raised.
+pilot_status pilot_server::complete(int p) {
     const double deadline = now_ms() + double(cfg.step_timeout_ms);
     for (;;) {
-        e = cudaStreamQuery(stream);
+        cudaError_t e = cudaEventQuery(step_done[p]);
         if (e == cudaSuccess) break;
         if (e != cudaErrorNotReady) return cuda_err(e, "serving step");
         if (now_ms() > deadline) return err(PILOT_ETIMEOUT, "a serving step ran longer than %lld ms",
                                             (long long)cfg.step_timeout_ms);
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    in_flight[p] = false;
     const double t = now_ms();
     std::lock_guard<std::mutex> lk(mu);
     ++steps;
@@ -267,7 +303,7 @@ void pilot_serve_config_default(pilot_serve_config* c) {
     c->max_slots = 4096;
     c->max_ef = 512;
     c->max_k = 100;
-    c->expansions_per_step = 64;
+    c->expansions_per_step = 256;
     c->max_new_per_step = 1024;
     c->queue_capacity = 1 << 20;
     c->step_timeout_ms = 10000;
@@ -338,20 +374,22 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((e = cudaMemset(S->state, 0, size_t(NS) * sizeof(SlotState))) != cudaSuccess) return cuda_err(e, "clear");
     if ((e = cudaMemset(S->stamps, 0, size_t(NS) * size_t(X.stamp_stride))) != cudaSuccess)
         return cuda_err(e, "clear");
-    if ((ps = S->halloc(&S->entries, size_t(NS))) != PILOT_OK) return ps;
-    if ((ps = S->halloc(&S->n_active, 1)) != PILOT_OK) return ps;
+    for (int p = 0; p < 2; ++p) {
+        if ((ps = S->halloc(&S->entries[p], size_t(NS))) != PILOT_OK) return ps;
+        if ((ps = S->halloc(&S->n_active[p], 1)) != PILOT_OK) return ps;
+        if ((ps = S->halloc(&S->staging_q[p], size_t(NN) * X.d)) != PILOT_OK) return ps;
+        if ((e = cudaEventCreateWithFlags(&S->step_done[p], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_err(e, "cudaEventCreate");
+    }
     if ((ps = S->halloc(&S->res_ids, size_t(NS) * c.max_k)) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_dists, size_t(NS) * c.max_k)) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_done, size_t(NS))) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_counters, size_t(NS) * 8)) != PILOT_OK) return ps;
-    if ((ps = S->halloc(&S->staging_q, size_t(NN) * X.d)) != PILOT_OK) return ps;
     if ((e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_err(e, "cudaStreamCreate");
 
-    // the step graph: reset the slot counter, run the step kernel
+    // the step graphs (one per parity): reset the slot counter, run the step kernel
     ServeIO sio{};
-    sio.entries = S->entries;
-    sio.n_active = S->n_active;
     sio.next = S->next;
     sio.state = S->state;
     sio.pool = S->pool;
@@ -375,19 +413,23 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     size_t smem = 0;
     if ((e = prepare_serve_step(XS, S->scfg, S->view.num_sms, NS, &blocks, &smem)) != cudaSuccess)
         return cuda_err(e, "size the step kernel");
-    cudaGraph_t g = nullptr;
-    if ((e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return cuda_err(e, "begin capture");
-    cudaError_t e1 = cudaMemsetAsync(S->next, 0, 4, S->stream);
-    cudaError_t e2 = launch_serve_step(XS, S->scfg, sio, S->stream, blocks, smem);
-    cudaError_t e3 = cudaStreamEndCapture(S->stream, &g);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return cuda_err(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "capture step graph");
+    for (int p = 0; p < 2; ++p) {
+        sio.entries = S->entries[p];
+        sio.n_active = S->n_active[p];
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_err(e, "begin capture");
+        cudaError_t e1 = cudaMemsetAsync(S->next, 0, 4, S->stream);
+        cudaError_t e2 = launch_serve_step(XS, S->scfg, sio, S->stream, blocks, smem);
+        cudaError_t e3 = cudaStreamEndCapture(S->stream, &g);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_err(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "capture step graph");
+        }
+        e = cudaGraphInstantiate(&S->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_err(e, "instantiate step graph");
     }
-    e = cudaGraphInstantiate(&S->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_err(e, "instantiate step graph");
     S->X = XS;
 
     S->slot_req.resize(size_t(NS));
