@@ -437,6 +437,54 @@ def run_forms(args):
     return 0
 
 
+def run_ablation(args):
+    """Component ablation in the manner of the paper's ablation table (Sec. 6.3):
+    at one ef, recall@10 and batch QPS of the full staged search, of FES seeds
+    T in {1, 4, 16}, without FES (the first entry), without stage (1)
+    (graceful degradation, Sec. 4.1) and without stage (2)'s expansions."""
+    import torch
+    from paper_2503_21206_b300 import pilot
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq)
+    nq, k = len(Q), w.k
+    ef = args.ef or 256
+    g = pilot.load_index_data(idx)
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    cnt = torch.empty((nq, 8), dtype=torch.int32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    kms = np.zeros(3, np.float32)
+    variants = [("staged (paper)", {}), ("fes_seeds=4", {"fes_seeds": 4}), ("fes_seeds=16", {"fes_seeds": 16}),
+                ("no FES (first entry)", {"use_fes": 0}), ("no stage (2) expansions", {"stage2_expansions": 0}),
+                ("no stage (1) (plain final stage)", {"stage1": 0, "stage2_expansions": 0})]
+    rows = []
+    for name, sw in variants:
+        opts = pilot.pilot_search_options_default()
+        for key, v in sw.items():
+            setattr(opts, key, v)
+
+        def search(counters=None):
+            return pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=opts, counters=counters,
+                                         kernel_ms=kms)
+
+        search(cnt)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt, k)
+        c = cnt.cpu().numpy().astype(np.float64)
+        step_ms, search_ms = timed_steps(search, stream, flush, args.steps, args.warmup, kms)
+        rows.append({"variant": name, "recall@10": round(rec, 5), "qps": nq / (step_ms / 1000.0),
+                     "search_kernel_ms": search_ms,
+                     "mean_counters": {n: round(float(c[:, i].mean()), 1) for i, n in
+                                       enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "ablation at fixed ef", "workload": args.workload, "n": idx.n, "nq": nq, "k": k,
+                      "ef": ef, "data": "synthetic", "rows": rows}), flush=True)
+    return 0
+
+
 def run_pilot(args):
     import torch
     ws, rank, local = dist_env()
@@ -613,6 +661,8 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-budget", type=int, default=256, help="expansions per request per step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--ablation", action="store_true",
+                    help="component ablation (FES seeds, stages on/off) at --ef (default 256)")
     ap.add_argument("--forms", action="store_true",
                     help="compare the reduced-row precision forms and the plain form (one GPU)")
     args = ap.parse_args(argv)
@@ -620,6 +670,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
     return run_forms(args) if args.forms else run_pilot(args)
 
 

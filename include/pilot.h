@@ -140,6 +140,11 @@ typedef struct {
     int32_t* status_words;      /* optional HOST array of 8 int32: [3] = queries whose FES
                                    survivors were not certified (the entry set was scanned
                                    exactly), [0] = non-finite queries; others reserved */
+    int32_t fes_seeds;          /* entries seeding stage (1)'s candidate list: the best
+                                   fes_seeds of the entry set by (reduced distance, id) with
+                                   FES, the first fes_seeds entries without it; capped at ef
+                                   and the entry count (default 1 = the paper's single entry;
+                                   1..16, PILOT_EINVAL otherwise; 0 reads as 1) */
 } pilot_search_options;
 
 void pilot_search_options_default(pilot_search_options* opt);

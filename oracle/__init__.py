@@ -47,7 +47,7 @@ class _Index(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("ef", ctypes.c_int), ("stage1", ctypes.c_int),
                 ("stage2_expansions", ctypes.c_int), ("stage3", ctypes.c_int),
-                ("use_fes", ctypes.c_int), ("nthreads", ctypes.c_int)]
+                ("use_fes", ctypes.c_int), ("fes_seeds", ctypes.c_int), ("nthreads", ctypes.c_int)]
 
 
 class _Outputs(ctypes.Structure):
@@ -115,9 +115,11 @@ class OracleIndex:
 
 
 def search(index: OracleIndex, queries: np.ndarray, k: int, ef: int, *, stage1: bool = True,
-           stage2_expansions: int = 2, stage3: bool = True, use_fes: bool = True,
+           stage2_expansions: int = 2, stage3: bool = True, use_fes: bool = True, fes_seeds: int = 1,
            nthreads: int = 1, pools: bool = False) -> dict:
-    """Staged PilotANN search (Sec. 4.1) of every query; returns a dict of arrays."""
+    """Staged PilotANN search (Sec. 4.1) of every query; returns a dict of arrays.
+    ``fes_seeds`` entries (the best by reduced distance with FES, the first of
+    the entry set without) seed stage (1); the paper uses one."""
     lib = _load()
     q = np.ascontiguousarray(queries, np.float32)
     nq = q.shape[0]
@@ -129,7 +131,7 @@ def search(index: OracleIndex, queries: np.ndarray, k: int, ef: int, *, stage1: 
     out = _Outputs(**{name: _ptr(res.get(name)) for name, _ in _Outputs._fields_})
     st, keep = index._struct()
     p = _Params(k=k, ef=ef, stage1=int(stage1), stage2_expansions=stage2_expansions, stage3=int(stage3),
-                use_fes=int(use_fes), nthreads=nthreads)
+                use_fes=int(use_fes), fes_seeds=fes_seeds, nthreads=nthreads)
     rc = lib.oracle_search(ctypes.byref(st), ctypes.byref(p), _ptr(q), ctypes.c_int64(nq), ctypes.byref(out))
     if rc != 0:
         raise ValueError("oracle_search rejected its arguments")

@@ -51,7 +51,8 @@ struct Params {
     int stage1;              // 1: run stage (1) on the subgraph (Sec. 4.1)
     int stage2_expansions;   // expansions of stage (2) on the subgraph (paper: 2)
     int stage3;              // 1: run stage (3) on the full graph
-    int use_fes;             // 1: dense FES over the entry set; 0: entry = entry_ids[0]
+    int use_fes;             // 1: dense FES over the entry set; 0: the first entries of entry_ids
+    int fes_seeds;           // entries seeding stage (1) (the paper: 1)
     int nthreads;
 };
 
@@ -215,24 +216,26 @@ void search_one(const Searcher& S, const Params& P, const float* query, int64_t 
     for (int64_t c = 0; c < ix.dp; ++c) qp[c] = double(float(qp[c]));
 
     // Fast entry selection, dense form (Sec. 5 / Table 2 "FES (1 block)"):
-    // the entry vector closest to q' by (distance, id).
-    Cand entry{0.0f, ix.entry_ids[0], false};
-    if (P.use_fes) {
-        bool have = false;
-        for (int64_t e = 0; e < ix.n_entry; ++e) {
-            Cand c{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false};
-            if (!have || cand_less(c, entry)) { entry = c; have = true; }
-        }
-    } else {
-        entry.dist = S.reduced_dist(qp.data(), entry.id, tmp.data());
-    }
+    // the entry vectors closest to q' by (distance, id) seed stage (1).  The
+    // paper seeds with the single closest one (fes_seeds = 1); more seeds are
+    // the top-T variant.  Without FES the seeds are the first entries of the
+    // set.  At most ef seeds.
+    const int64_t ns = std::min<int64_t>(std::min<int64_t>(P.fes_seeds, P.ef), ix.n_entry);
+    std::vector<Cand> seeds;
+    const int64_t n_scored = P.use_fes ? ix.n_entry : ns;
+    for (int64_t e = 0; e < n_scored; ++e)
+        seeds.push_back(Cand{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false});
+    std::sort(seeds.begin(), seeds.end(), cand_less);
+    seeds.resize(size_t(ns));
+    const Cand entry = seeds[0];
 
     Counters c1, c2, c3;
     std::vector<uint8_t> visited(ix.n, 0);
 
-    // Stage (1): Algorithm 1 over the subgraph with reduced distances.
-    std::vector<Cand> C{entry};
-    visited[entry.id] = 1;
+    // Stage (1): Algorithm 1 over the subgraph with reduced distances, from
+    // the seeds (all unchecked, all visited).
+    std::vector<Cand> C = seeds;
+    for (const Cand& c : C) visited[c.id] = 1;
     if (P.stage1) {
         greedy_search(C, visited, ix.R_sub,
                       [&](int32_t u) { return ix.subgraph + int64_t(u) * ix.R_sub; },
@@ -321,7 +324,7 @@ extern "C" {
 // Staged search of Sec. 4.1 over nq queries (nq x d FP32, row-major).
 // Returns 0 on success, -1 on invalid arguments.
 int oracle_search(const Index* ix, const Params* P, const float* queries, int64_t nq, const Outputs* out) {
-    if (!ix || !P || P->k < 1 || P->ef < P->k || ix->n_entry < 1) return -1;
+    if (!ix || !P || P->k < 1 || P->ef < P->k || ix->n_entry < 1 || P->fes_seeds < 1) return -1;
     Searcher S(*ix);
     parallel_for(nq, P->nthreads, [&](int64_t qi) { search_one(S, *P, queries + qi * ix->d, qi, *out); });
     return 0;

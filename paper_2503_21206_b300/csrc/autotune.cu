@@ -81,6 +81,7 @@ extern "C" pilot_status pilot_autotune(pilot_index* index, const float* queries,
         stages.stage2_expansions = base->stage2_expansions;
         stages.stage3 = base->stage3;
         stages.use_fes = base->use_fes;
+        stages.fes_seeds = base->fes_seeds;
     }
     const std::string key = tune_key(*v.dev, v.device, cls) + "|s" + std::to_string(stages.stage1 != 0) + "." +
                             std::to_string(stages.stage2_expansions) + "." + std::to_string(stages.stage3 != 0) +

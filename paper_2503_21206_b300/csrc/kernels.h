@@ -47,6 +47,7 @@ struct SearchConfig {
     int stage1, stage2_expansions, stage3, use_fes;
     int warps_per_block;
     int fes_T;
+    int fes_seeds;       // entries seeding stage (1) (1..kFesT)
     int stage_bytes;     // per-warp row staging buffer
 };
 

@@ -128,7 +128,7 @@ extern "C" {
 
 const char* pilot_last_error(void) { return g_error.c_str(); }
 
-int pilot_abi_version(void) { return 1; }
+int pilot_abi_version(void) { return 2; }
 
 void pilot_search_options_default(pilot_search_options* opt) {
     if (!opt) return;
@@ -137,6 +137,7 @@ void pilot_search_options_default(pilot_search_options* opt) {
     opt->stage2_expansions = 2;
     opt->stage3 = 1;
     opt->use_fes = 1;
+    opt->fes_seeds = 1;
 }
 
 void pilot_index_free(pilot_index* index) { delete index; }
@@ -458,6 +459,9 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     pilot_search_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.stage2_expansions < 0) return fail(PILOT_EINVAL, "stage2_expansions < 0");
+    if (opt.fes_seeds == 0) opt.fes_seeds = 1;
+    if (opt.fes_seeds < 1 || opt.fes_seeds > kFesT)
+        return fail(PILOT_EINVAL, "fes_seeds = %d outside [1, %d]", opt.fes_seeds, kFesT);
     if (nq == 0) return PILOT_OK;
     std::lock_guard<std::mutex> lock(ix->mu);
     CUDA_TRY(cudaSetDevice(ix->device));
@@ -469,6 +473,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cfg.stage2_expansions = opt.stage2_expansions;
     cfg.stage3 = opt.stage3 != 0;
     cfg.use_fes = opt.use_fes != 0;
+    cfg.fes_seeds = opt.fes_seeds;
     // explicit options first, then the autotuned shape of this ef class, then the defaults
     const TunedShape& tuned = ix->tuned[ef_class(ef)];
     const int wpb = opt.warps_per_block > 0 ? opt.warps_per_block : tuned.warps_per_block;

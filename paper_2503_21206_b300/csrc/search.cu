@@ -568,12 +568,20 @@ struct Searcher {
         __syncwarp();
     }
 
-    // Fast entry selection: exact distances of the scoring survivors; if the
-    // best of them is not certified below the bound on all other entries,
-    // an exact scan of the whole entry set (Sec. 5, dense form).
+    // Fast entry selection (Sec. 5, dense form) seeding stage (1) with the
+    // best `ns` entries by (reduced distance, id): exact distances of the
+    // scoring survivors, sorted; if the ns-th of them is not certified below
+    // the bound on every other entry, an exact scan of the whole entry set
+    // keeps the best ns (merged into C with ef = ns).  Without FES the seeds
+    // are the first ns entries of the set.
     __device__ void fes(QState& st, const int32_t* fes_pos, double fes_lb) {
         const int lane = w.lane;
-        uint64_t best;
+        int ns = cfg.fes_seeds < w.ef ? cfg.fes_seeds : w.ef;
+        if (int64_t(ns) > ix.n_entry) ns = int(ix.n_entry);
+        new_visited_set(w, ix.stamp_stride);
+        w.S = 0;
+        w.lb = 0;
+        bool scan = false;
         if (cfg.use_fes) {
             const int T = cfg.fes_T;
             const int32_t p = lane < T ? fes_pos[lane] : -1;
@@ -584,37 +592,48 @@ struct Searcher {
             __syncwarp();
             reduced_batch(m);
             __syncwarp();
-            best = warp_min(lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
-            const float dstar = key_dist(best);
-            if (!(fes_lb >= double(nextafterf(dstar, INFINITY)))) {
-                st.fallback = 1;
-                best = kKeyEmpty;
-                for (int64_t e0 = 0; e0 < ix.n_entry; e0 += kCand) {
-                    const int mm = ix.n_entry - e0 < kCand ? int(ix.n_entry - e0) : kCand;
-                    if (lane < mm) w.cand[lane] = __ldg(ix.entry + e0 + lane);
-                    __syncwarp();
-                    reduced_batch(mm);
-                    __syncwarp();
-                    const uint64_t b = warp_min(lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
-                    best = b < best ? b : best;
-                    __syncwarp();
-                }
+            const uint64_t key = warp_sort32(lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
+            const uint64_t kth = __shfl_sync(kFull, key, ns - 1);
+            if (m >= ns && fes_lb >= double(nextafterf(key_dist(kth), INFINITY))) {
+                if (lane < ns) w.pool[lane] = key;
+                w.S = ns;
+            } else {
+                scan = true;
             }
         } else {
-            if (lane == 0) w.cand[0] = __ldg(ix.entry);
+            if (lane < ns) w.cand[lane] = __ldg(ix.entry + lane);
             __syncwarp();
-            reduced_batch(1);
+            reduced_batch(ns);
             __syncwarp();
-            best = make_key(w.dist[0], w.cand[0]);
+            const uint64_t key = warp_sort32(lane < ns ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
+            if (lane < ns) w.pool[lane] = key;
+            w.S = ns;
         }
-        st.best = best;
-        // stage (1) starts from the entry alone, visited = {entry}
-        new_visited_set(w, ix.stamp_stride);
-        if (lane == 0) {
-            w.pool[0] = best;
-            w.stamps[key_id(best)] = uint8_t(w.epoch);
+        if (scan) {
+            st.fallback = 1;
+            const int ef_keep = w.ef;
+            w.ef = ns;
+            for (int64_t e0 = 0; e0 < ix.n_entry; e0 += kCand) {
+                const int mm = ix.n_entry - e0 < kCand ? int(ix.n_entry - e0) : kCand;
+                if (lane < mm) w.cand[lane] = __ldg(ix.entry + e0 + lane);
+                __syncwarp();
+                reduced_batch(mm);
+                __syncwarp();
+                uint64_t k = lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
+                if (w.S == w.ef && k >= w.pool[w.S - 1]) k = kKeyEmpty;
+                const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
+                if (nkeep > 0) {
+                    k = warp_sort32(k, lane);
+                    merge_new(w, k, nkeep, ns);
+                }
+                __syncwarp();
+            }
+            w.ef = ef_keep;
         }
-        w.S = 1;
+        __syncwarp();
+        st.best = w.pool[0];
+        // stage (1) starts from the seeds, all unchecked; visited = the seeds
+        if (lane < w.S) w.stamps[key_id(w.pool[lane])] = uint8_t(w.epoch);
         w.lb = 0;
         st.phase = kStage1;
         st.it = 0;
@@ -961,6 +980,7 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.stage3 = 1;
     cfg.use_fes = 1;
     cfg.fes_T = kFesT;
+    cfg.fes_seeds = 1;
     cfg.warps_per_block = 2;
     int stage = 4 * (ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes);
     const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;

@@ -44,7 +44,8 @@ class pilot_index_desc(ctypes.Structure):
 class pilot_search_options(ctypes.Structure):
     _fields_ = [("stage1", ctypes.c_int32), ("stage2_expansions", ctypes.c_int32), ("stage3", ctypes.c_int32),
                 ("use_fes", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("stage_rows", ctypes.c_int32),
-                ("counters", ctypes.c_void_p), ("kernel_ms", ctypes.c_void_p), ("status_words", ctypes.c_void_p)]
+                ("counters", ctypes.c_void_p), ("kernel_ms", ctypes.c_void_p), ("status_words", ctypes.c_void_p),
+                ("fes_seeds", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

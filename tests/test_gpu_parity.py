@@ -235,6 +235,58 @@ def test_wide_rows_multi_pass(pilot, torch_cuda, stage_rows):
     assert np.array_equal(cnt, ref["counters"])
 
 
+@pytest.mark.parametrize("T", [2, 5, 16])
+def test_fes_seeds_parity(c1, pilot, torch_cuda, T):
+    """Top-T FES seeding: the GPU seeds stage (1) with the same T entries and
+    then follows the same path."""
+    w, idx, Q, _, g = c1
+    ref = oracle.search(oracle_index(idx), Q, 10, 64, fes_seeds=T)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 64, fes_seeds=T)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+def test_fes_seeds_without_fes_and_inner_product(pilot, torch_cuda):
+    w = synth.WORKLOADS["c3_powerlaw_2m_d768"]
+    idx, Q, _, _ = index_build.build_workload(w, n=5000, nq=24, reduced_dtype="bf16")
+    g = pilot.load_index_data(idx)
+    for use_fes, T in ((True, 4), (False, 3)):
+        ref = oracle.search(oracle_index(idx), Q, 10, 48, use_fes=use_fes, fes_seeds=T)
+        ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 48, use_fes=use_fes, fes_seeds=T)
+        assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+        assert np.array_equal(cnt, ref["counters"])
+
+
+def test_fes_seed_ties_take_the_exact_scan(pilot, torch_cuda):
+    """Entries with identical vectors tie on distance: the 16 scored survivors
+    cannot certify the T best, so the warp scans the entry set exactly and
+    breaks the ties by id, like the oracle."""
+    rng = np.random.default_rng(11)
+    base = rng.standard_normal((12, 96)).astype(np.float32)
+    X = np.repeat(base, 200, axis=0)           # 2400 rows, each vector 200 times (~50 entries each)
+    Q = (base + 0.05 * rng.standard_normal((12, 96))).astype(np.float32)
+    idx = index_build.build_index(X, 16, 16, 0.5, 32, 600, 0, 5, 6, "f32")
+    g = pilot.load_index_data(idx)
+    for T in (1, 8):
+        ref = oracle.search(oracle_index(idx), Q, 10, 32, fes_seeds=T)
+        o = pilot.pilot_search_options_default()
+        o.fes_seeds = T
+        status = np.zeros(8, np.int32)
+        o.status_words = status.ctypes.data
+        cnt = np.empty((len(Q), 8), np.int32)
+        ids, dists = pilot.pilot_search_ex(g, Q, 10, 32, options=o, counters=cnt)
+        assert status[3] > 0, "no query took the exact entry scan"
+        assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+        assert np.array_equal(cnt, ref["counters"])
+
+
+def test_fes_seeds_out_of_range(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    for bad in (-1, 17):
+        with pytest.raises(pilot.PilotError):
+            gpu_search(pilot, torch_cuda, g, Q[:4], 10, 64, fes_seeds=bad)
+
+
 def test_load_from_files(c1, pilot, torch_cuda, tmp_path):
     w, idx, Q, _, g = c1
     index_build.save_index(idx, str(tmp_path))

@@ -203,6 +203,35 @@ def test_dense_fes_is_argmin_over_entries(c1_small):
         assert dist[i] == dd[j]
 
 
+@pytest.mark.parametrize("T", [1, 3, 16])
+@pytest.mark.parametrize("use_fes", [True, False])
+def test_fes_seeds_are_the_best_entries(c1_small, T, use_fes):
+    """Top-T seeding: stage (1) starts from the T entries closest to q' by
+    (reduced FP32 distance, id) -- the first T of the entry set without FES --
+    all of them visited.  With every stage off, C after stage (1) is exactly
+    those seeds, checked here against a numpy brute force over the entries."""
+    idx, Q, red32, _ = c1_small
+    ix = oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, 0, None,
+                            idx.full, idx.entry_ids, 0)
+    r = oracle.search(ix, Q, 10, 64, stage1=False, stage2_expansions=0, stage3=False, use_fes=use_fes,
+                      fes_seeds=T, pools=True)
+    _, qp = oracle.project(ix, Q)
+    sub_ids = np.nonzero(idx.subgraph_mask)[0]
+    row_of = {int(v): i for i, v in enumerate(sub_ids)}
+    ent = idx.entry_ids if use_fes else idx.entry_ids[:T]
+    E = np.asarray([red32[row_of[int(e)]] for e in ent], np.float64)
+    for i in range(len(Q)):
+        dd = ((qp[i].astype(np.float64) - E) ** 2).sum(1).astype(np.float32)
+        order = np.lexsort((ent, dd))[:T]
+        assert r["pool1_ids"][i, :T].tolist() == ent[order].tolist()
+        np.testing.assert_array_equal(r["pool1_dists"][i, :T], dd[order])
+        assert np.all(r["pool1_ids"][i, T:] == -1)
+        assert r["counters"][i, 7] == ent[order[0]]
+    # with stage (1) on, every seed and every new stage-(1) distance is re-ranked (up to ef)
+    r = oracle.search(ix, Q, 10, 64, use_fes=use_fes, fes_seeds=T)
+    assert np.all(r["counters"][:, 6] == np.minimum(64, r["counters"][:, 1] + T))
+
+
 def test_graceful_degradation(c1_small):
     """Sec. 4.1 'Summary': with stages (1) and (2) off, the search is plain
     greedy search over the full graph from the FES entry.  With ef >= reach
