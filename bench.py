@@ -598,6 +598,11 @@ def run_pilot(args):
     if not args.no_serving:
         serving = serving_run(pilot, g, Q, gt, args.serve_rate, args.serve_requests, max_ef=512, max_k=100,
                               expansions_per_step=args.serve_budget)
+        # capacity: the operating point's k and ef offered at twice the batch rate
+        cap_rate = 2.0 * aggregate_throughput(nq * args.steps, 1, sum(step_ms) / 1000.0)
+        serving["capacity"] = serving_run(pilot, g, Q, gt, cap_rate, min(int(cap_rate * 0.5), 150_000),
+                                          fixed_ef=ef, max_ef=512, max_k=100,
+                                          expansions_per_step=args.serve_budget)
     peak, peak_kind = measured_peaks()
     mean_search_ms = statistics.mean(search_ms)
     achieved = alg_bytes / (mean_search_ms / 1000.0) / 1e9
@@ -659,7 +664,7 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) run")
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-requests", type=int, default=100_000)
-    ap.add_argument("--serve-budget", type=int, default=256, help="expansions per request per step")
+    ap.add_argument("--serve-budget", type=int, default=1024, help="expansions per request per step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--ablation", action="store_true",
                     help="component ablation (FES seeds, stages on/off) at --ef (default 256)")

@@ -203,15 +203,17 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
  * max_slots or what hbm_budget_bytes holds (list, query rows and one visited
- * byte per node per slot), whichever is smaller; further requests queue, and
+ * byte per node per slot), whichever is smaller, rounded down to a multiple
+ * of the warps the step kernel keeps resident (when it holds at least one
+ * such wave), so that every step runs whole waves; further requests queue, and
  * submit returns PILOT_EBUSY when queue_capacity requests are waiting.
  */
 typedef struct {
     int32_t max_slots;            /* requests in flight at most (default 4096) */
     int32_t max_ef;               /* largest ef a request may use (default 512) */
     int32_t max_k;                /* largest k (default 100) */
-    int32_t expansions_per_step;  /* per request per step (default 256) */
-    int32_t max_new_per_step;     /* admissions per step (default 1024) */
+    int32_t expansions_per_step;  /* per request per step (default 512) */
+    int32_t max_new_per_step;     /* admissions per step (default 8192; at most the slot count) */
     int32_t step_timeout_ms;      /* a step longer than this fails the server (default 10000) */
     int64_t queue_capacity;       /* waiting requests before PILOT_EBUSY (default 2^20) */
     int64_t hbm_budget_bytes;     /* device memory for slots; 0 = a quarter of free memory */

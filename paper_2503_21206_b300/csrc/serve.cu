@@ -303,8 +303,8 @@ void pilot_serve_config_default(pilot_serve_config* c) {
     c->max_slots = 4096;
     c->max_ef = 512;
     c->max_k = 100;
-    c->expansions_per_step = 256;
-    c->max_new_per_step = 1024;
+    c->expansions_per_step = 512;
+    c->max_new_per_step = 8192;
     c->queue_capacity = 1 << 20;
     c->step_timeout_ms = 10000;
 }
@@ -354,7 +354,16 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     const int64_t fit = int64_t(budget / per_slot);
     S->slots = int(std::min<int64_t>(c.max_slots, fit));
     if (S->slots < 1) return err(PILOT_ENOMEM, "the HBM budget holds no slot (%lld bytes per slot)", (long long)per_slot);
-    const int NS = S->slots, NN = c.max_new_per_step;
+    {   // whole waves: a multiple of the step kernel's resident warps, so no step ends on a partial wave
+        int all_blocks = 0;
+        size_t smem_probe = 0;
+        if ((e = prepare_serve_step(X, S->scfg, S->view.num_sms, 1 << 30, &all_blocks, &smem_probe)) != cudaSuccess)
+            return cuda_err(e, "size the step kernel");
+        const int resident = all_blocks * S->scfg.warps_per_block;
+        if (resident > 0 && S->slots >= resident) S->slots -= S->slots % resident;
+    }
+    const int NS = S->slots, NN = std::min<int>(c.max_new_per_step, S->slots);
+    S->cfg.max_new_per_step = NN;
 
     pilot_status ps;
     if ((ps = S->dalloc(&S->state, size_t(NS))) != PILOT_OK) return ps;
