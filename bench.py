@@ -437,6 +437,119 @@ def run_forms(args):
     return 0
 
 
+def run_serve_sweep(args):
+    """The serving configuration: Poisson arrivals of mixed k in {1, 10, 100}
+    and ef in 32..512 at several offered rates, p50/p99 latency and served
+    QPS at each, beside the batch operating point of the same index."""
+    import torch
+    from paper_2503_21206_b300 import pilot
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq)
+    g = pilot.load_index_data(idx)
+    nq, k = len(Q), w.k
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    kms = np.zeros(3, np.float32)
+    batch = []
+    for ef in (64, 128, 256, 512):
+        pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, kernel_ms=kms)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt, k)
+        step_ms, search_ms = timed_steps(lambda: pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream,
+                                                                       kernel_ms=kms),
+                                         stream, flush, args.steps, args.warmup, kms)
+        batch.append({"ef": ef, "recall@10": round(rec, 5), "qps": nq / (step_ms / 1000.0)})
+    rows = []
+    for rate in rates:
+        r = serving_run(pilot, g, Q, gt, rate, min(int(rate * 2.0), args.serve_requests), max_ef=512, max_k=100,
+                        expansions_per_step=args.serve_budget)
+        rows.append(r)
+        print(json.dumps(r), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "serving p50/p99 and QPS by offered rate", "workload": args.workload, "n": idx.n,
+                      "d": idx.d, "dp": idx.dp, "reduced_dtype": idx.reduced_dtype, "nq": nq,
+                      "data": "synthetic", "budget": args.serve_budget, "batch": batch, "serving": rows}),
+          flush=True)
+    return 0
+
+
+def run_tau(args):
+    """The analysis of Sec. 4.2 (its tau/ef figures) on synthetic data: the
+    final stage alone (Algorithm 1 on the full graph with full vectors),
+    its candidate list of size ef seeded with tau true neighbours plus
+    ef - tau random nodes.  For each tau/ef and ef: recall@10 and the
+    distance calculations per query (seeds scored + new distances).  Then
+    the calculations needed for recall@10 = 0.9 (interpolated over ef), the
+    saving against tau = 0, and the acceleration threshold: the smallest
+    tau/ef with a 2x saving."""
+    import torch
+    from paper_2503_21206_b300 import index_build, pilot
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    w, idx, Q, gt10 = load_workload(args.workload, args.n, args.nq)
+    Q = Q[: min(len(Q), 2000)]
+    gt10 = gt10[: len(Q)]
+    nq, k = len(Q), w.k
+    efs = (32, 64, 128, 256, 512)
+    fracs = (0.0, 1 / 16, 1 / 8, 3 / 16, 1 / 4)
+    gt, _ = index_build.exact_topk(idx.full, Q, int(max(efs) * max(fracs)), metric=idx.metric, device="cuda")
+    g = pilot.load_index_data(idx)
+    rng = np.random.default_rng(7)
+    curves = []
+    for f in fracs:
+        pts = []
+        for ef in efs:
+            tau = int(round(f * ef))
+            seeds = np.empty((nq, ef), np.int32)
+            for i in range(nq):
+                known = gt[i, :tau]
+                cand = rng.choice(idx.n, size=ef + tau, replace=False)
+                rest = cand[~np.isin(cand, known)][: ef - tau]
+                seeds[i, :tau] = known
+                seeds[i, tau:] = rest
+            o = pilot.pilot_search_options_default()
+            o.stage1, o.stage2_expansions = 0, 0
+            o.seed_ids, o.seed_count = seeds.ctypes.data, ef
+            cnt = np.empty((nq, 8), np.int32)
+            ids, _ = pilot.pilot_search_ex(g, Q, k, ef, options=o, counters=cnt)
+            calcs = float((cnt[:, 5] + cnt[:, 6]).mean())
+            pts.append({"ef": ef, "tau": tau, "recall@10": round(recall_at_k(ids, gt10, k), 5),
+                        "calcs_per_query": round(calcs, 1), "expansions": round(float(cnt[:, 4].mean()), 1)})
+        curves.append({"tau_over_ef": f, "points": pts})
+        print(json.dumps(curves[-1]), file=sys.stderr, flush=True)
+
+    def calcs_at(points, target):
+        xs = [p["recall@10"] for p in points]
+        ys = [p["calcs_per_query"] for p in points]
+        for j in range(1, len(xs)):
+            if xs[j - 1] < target <= xs[j]:
+                return ys[j - 1] + (ys[j] - ys[j - 1]) * (target - xs[j - 1]) / (xs[j] - xs[j - 1])
+        return ys[0] if xs and xs[0] >= target else None
+
+    target = 0.9
+    base = calcs_at(curves[0]["points"], target)
+    savings = []
+    for c in curves:
+        v = calcs_at(c["points"], target)
+        savings.append({"tau_over_ef": c["tau_over_ef"], "calcs_at_recall": v,
+                        "fraction_of_tau0": None if (v is None or not base) else round(v / base, 4)})
+    threshold = None
+    for a, b in zip(savings, savings[1:]):
+        fa, fb = a["fraction_of_tau0"], b["fraction_of_tau0"]
+        if fa is not None and fb is not None and fa > 0.5 >= fb:
+            threshold = a["tau_over_ef"] + (b["tau_over_ef"] - a["tau_over_ef"]) * (fa - 0.5) / (fa - fb)
+            break
+    print(json.dumps({"metric": "distance calculations vs recall by tau/ef (final stage alone)",
+                      "workload": args.workload, "n": idx.n, "d": idx.d, "nq": nq, "recall_target": target,
+                      "curves": curves, "savings": savings, "acceleration_threshold_2x": threshold,
+                      "data": "synthetic"}), flush=True)
+    return 0
+
+
 def run_ablation(args):
     """Component ablation in the manner of the paper's ablation table (Sec. 6.3):
     at one ef, recall@10 and batch QPS of the full staged search, of FES seeds
@@ -666,6 +779,11 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-budget", type=int, default=1024, help="expansions per request per step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving at each of --serve-rates (mixed k and ef) beside the batch operating points")
+    ap.add_argument("--serve-rates", default="20000,50000,100000,200000")
+    ap.add_argument("--tau", action="store_true",
+                    help="the tau/ef analysis: final stage seeded with tau true neighbours + random nodes")
     ap.add_argument("--ablation", action="store_true",
                     help="component ablation (FES seeds, stages on/off) at --ef (default 256)")
     ap.add_argument("--forms", action="store_true",
@@ -677,6 +795,10 @@ def main(argv=None):
         return run_reference(args)
     if args.ablation:
         return run_ablation(args)
+    if args.serve_sweep:
+        return run_serve_sweep(args)
+    if args.tau:
+        return run_tau(args)
     return run_forms(args) if args.forms else run_pilot(args)
 
 

@@ -145,6 +145,15 @@ typedef struct {
                                    FES, the first fes_seeds entries without it; capped at ef
                                    and the entry count (default 1 = the paper's single entry;
                                    1..16, PILOT_EINVAL otherwise; 0 reads as 1) */
+    const int32_t* seed_ids;    /* optional HOST array nq x seed_count of original ids that
+                                   replace FES and seed the final stage alone (the experiment
+                                   of Sec. 4.2: tau known neighbours plus random nodes):
+                                   requires stage1 = 0, stage2_expansions = 0, stage3 = 1;
+                                   C starts as the row's ids with full distances, all
+                                   unchecked and visited; -1 entries are skipped; ids must be
+                                   < n and distinct within a row (PILOT_EINVAL otherwise).
+                                   Counters: [6] = seeds scored, [7] = -1 */
+    int32_t seed_count;         /* entries per row of seed_ids, 1..ef */
 } pilot_search_options;
 
 void pilot_search_options_default(pilot_search_options* opt);

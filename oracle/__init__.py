@@ -47,7 +47,8 @@ class _Index(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("ef", ctypes.c_int), ("stage1", ctypes.c_int),
                 ("stage2_expansions", ctypes.c_int), ("stage3", ctypes.c_int),
-                ("use_fes", ctypes.c_int), ("fes_seeds", ctypes.c_int), ("nthreads", ctypes.c_int)]
+                ("use_fes", ctypes.c_int), ("fes_seeds", ctypes.c_int), ("nthreads", ctypes.c_int),
+                ("seed_count", ctypes.c_int), ("seed_ids", ctypes.c_void_p)]
 
 
 class _Outputs(ctypes.Structure):
@@ -116,10 +117,12 @@ class OracleIndex:
 
 def search(index: OracleIndex, queries: np.ndarray, k: int, ef: int, *, stage1: bool = True,
            stage2_expansions: int = 2, stage3: bool = True, use_fes: bool = True, fes_seeds: int = 1,
-           nthreads: int = 1, pools: bool = False) -> dict:
+           nthreads: int = 1, pools: bool = False, seed_ids: np.ndarray | None = None) -> dict:
     """Staged PilotANN search (Sec. 4.1) of every query; returns a dict of arrays.
     ``fes_seeds`` entries (the best by reduced distance with FES, the first of
-    the entry set without) seed stage (1); the paper uses one."""
+    the entry set without) seed stage (1); the paper uses one.  ``seed_ids``
+    (nq x T original ids, -1 skipped) instead seeds the final stage alone
+    (the experiment of Sec. 4.2); the other stage options are then ignored."""
     lib = _load()
     q = np.ascontiguousarray(queries, np.float32)
     nq = q.shape[0]
@@ -132,7 +135,14 @@ def search(index: OracleIndex, queries: np.ndarray, k: int, ef: int, *, stage1: 
     st, keep = index._struct()
     p = _Params(k=k, ef=ef, stage1=int(stage1), stage2_expansions=stage2_expansions, stage3=int(stage3),
                 use_fes=int(use_fes), fes_seeds=fes_seeds, nthreads=nthreads)
+    seeds = None
+    if seed_ids is not None:
+        seeds = np.ascontiguousarray(seed_ids, np.int32)
+        assert seeds.shape[0] == nq and seeds.ndim == 2
+        p.seed_count = seeds.shape[1]
+        p.seed_ids = seeds.ctypes.data
     rc = lib.oracle_search(ctypes.byref(st), ctypes.byref(p), _ptr(q), ctypes.c_int64(nq), ctypes.byref(out))
+    del seeds
     if rc != 0:
         raise ValueError("oracle_search rejected its arguments")
     del keep

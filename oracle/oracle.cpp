@@ -54,6 +54,8 @@ struct Params {
     int use_fes;             // 1: dense FES over the entry set; 0: the first entries of entry_ids
     int fes_seeds;           // entries seeding stage (1) (the paper: 1)
     int nthreads;
+    int seed_count;          // with seed_ids: entries per query row
+    const int32_t* seed_ids; // nq x seed_count original ids seeding the final stage alone, or null
 };
 
 // Per-query outputs.  Any pointer may be null.
@@ -231,6 +233,36 @@ void search_one(const Searcher& S, const Params& P, const float* query, int64_t 
 
     Counters c1, c2, c3;
     std::vector<uint8_t> visited(ix.n, 0);
+
+    // The experiment of Sec. 4.2: the final stage alone (Algorithm 1 on the
+    // full graph), its candidate list seeded with given nodes (known true
+    // neighbours plus random ones), all unchecked and visited.
+    if (P.seed_ids) {
+        std::vector<Cand> C;
+        int32_t scored = 0;
+        for (int j = 0; j < P.seed_count; ++j) {
+            const int32_t v = P.seed_ids[qi * P.seed_count + j];
+            if (v < 0 || visited[v]) continue;
+            visited[v] = 1;
+            C.push_back(Cand{S.full_dist(q.data(), v, tmp.data()), v, false});
+            scored += 1;
+        }
+        std::sort(C.begin(), C.end(), cand_less);
+        if (C.size() > size_t(P.ef)) C.resize(size_t(P.ef));
+        greedy_search(C, visited, ix.R, [&](int32_t u) { return ix.graph + int64_t(u) * ix.R; },
+                      [&](int32_t v) { return S.full_dist(q.data(), v, tmp.data()); }, P.ef, INT64_MAX, c3);
+        for (int j = 0; j < P.k; ++j) {
+            const bool ok = size_t(j) < C.size();
+            if (out.ids) out.ids[qi * P.k + j] = ok ? C[j].id : -1;
+            if (out.dists) out.dists[qi * P.k + j] = ok ? C[j].dist : INFINITY;
+        }
+        if (out.counters) {
+            int32_t* k = out.counters + qi * 8;
+            k[0] = k[1] = k[2] = k[3] = 0;
+            k[4] = c3.exp; k[5] = c3.dist; k[6] = scored; k[7] = -1;
+        }
+        return;
+    }
 
     // Stage (1): Algorithm 1 over the subgraph with reduced distances, from
     // the seeds (all unchecked, all visited).

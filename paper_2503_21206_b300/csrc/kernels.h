@@ -66,6 +66,8 @@ struct SearchIO {
     int32_t* bad_query;        // nq flags (non-finite input)
     int32_t* status;           // [0] non-finite queries, [1] next query, [2] gather timeouts,
                                // [3] FES fallbacks, [4] expansion-cap hits, [5] FES kernel timeouts
+    const int32_t* seed_ids;   // nq x seed_count original ids (-1 skipped) seeding the final stage, or null
+    int seed_count;
 };
 
 // ------------------------------------------------------------- serving --

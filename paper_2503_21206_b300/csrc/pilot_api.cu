@@ -462,6 +462,28 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (opt.fes_seeds == 0) opt.fes_seeds = 1;
     if (opt.fes_seeds < 1 || opt.fes_seeds > kFesT)
         return fail(PILOT_EINVAL, "fes_seeds = %d outside [1, %d]", opt.fes_seeds, kFesT);
+    if (opt.seed_ids) {
+        if (opt.stage1 || opt.stage2_expansions != 0 || !opt.stage3)
+            return fail(PILOT_EINVAL, "seed_ids seed the final stage alone: stage1 = 0, stage2_expansions = 0, "
+                                      "stage3 = 1");
+        if (opt.seed_count < 1 || opt.seed_count > ef)
+            return fail(PILOT_EINVAL, "seed_count = %d outside [1, ef = %d]", opt.seed_count, ef);
+        if (is_device_ptr(opt.seed_ids)) return fail(PILOT_EINVAL, "seed_ids must be host memory");
+        std::vector<int32_t> row(size_t(opt.seed_count));
+        for (int64_t q = 0; q < nq; ++q) {
+            const int32_t* r = opt.seed_ids + q * opt.seed_count;
+            size_t n_ok = 0;
+            for (int j = 0; j < opt.seed_count; ++j) {
+                if (r[j] == -1) continue;
+                if (r[j] < 0 || int64_t(r[j]) >= ix->dev.n)
+                    return fail(PILOT_EINVAL, "seed id %d of query %lld out of range", r[j], (long long)q);
+                row[n_ok++] = r[j];
+            }
+            std::sort(row.begin(), row.begin() + n_ok);
+            if (std::adjacent_find(row.begin(), row.begin() + n_ok) != row.begin() + n_ok)
+                return fail(PILOT_EINVAL, "seed ids of query %lld repeat", (long long)q);
+        }
+    }
     if (nq == 0) return PILOT_OK;
     std::lock_guard<std::mutex> lock(ix->mu);
     CUDA_TRY(cudaSetDevice(ix->device));
@@ -503,6 +525,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     const size_t o_ids = ids_dev ? 0 : take(size_t(nq) * k * 4);
     const size_t o_dists = dists_dev ? 0 : take(size_t(nq) * k * 4);
     const size_t o_cnt = (opt.counters && !cnt_dev) ? take(size_t(nq) * 8 * 4) : 0;
+    const size_t o_seed = opt.seed_ids ? take(size_t(nq) * opt.seed_count * 4) : 0;
     if (off > ix->ws_bytes) {
         if (ix->ws) cudaFree(ix->ws);
         ix->ws = nullptr;
@@ -524,10 +547,15 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     io.out_ids = ids_dev ? out_ids : reinterpret_cast<int32_t*>(ws + o_ids);
     io.out_dists = dists_dev ? out_dists : reinterpret_cast<float*>(ws + o_dists);
     io.counters = opt.counters ? (cnt_dev ? opt.counters : reinterpret_cast<int32_t*>(ws + o_cnt)) : nullptr;
+    io.seed_ids = opt.seed_ids ? reinterpret_cast<const int32_t*>(ws + o_seed) : nullptr;
+    io.seed_count = opt.seed_ids ? opt.seed_count : 0;
 
     CUDA_TRY(cudaMemsetAsync(io.status, 0, 8 * 4, st));
     if (!q_dev)
         CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(io.queries), queries, size_t(nq) * X.d * 4,
+                                 cudaMemcpyHostToDevice, st));
+    if (opt.seed_ids)
+        CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t*>(io.seed_ids), opt.seed_ids, size_t(nq) * opt.seed_count * 4,
                                  cudaMemcpyHostToDevice, st));
     const bool timed = opt.kernel_ms != nullptr;
     if (timed && !ix->ev[0])
@@ -535,7 +563,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[0], st));
     CUDA_TRY(launch_project(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[1], st));
-    if (cfg.use_fes) CUDA_TRY(launch_fes_mma(X, io, st));
+    if (cfg.use_fes && !opt.seed_ids) CUDA_TRY(launch_fes_mma(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[2], st));
     {
         cudaError_t e = launch_search(X, cfg, io, st, ix->num_sms);
@@ -561,6 +589,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (S[2]) return fail(PILOT_ETIMEOUT, "%d search warps gave up waiting for a row gather", S[2]);
     if (S[5]) return fail(PILOT_ETIMEOUT, "%d FES blocks gave up waiting for the tensor cores", S[5]);
     if (S[4]) return fail(PILOT_ECUDA, "%d queries hit the expansion cap", S[4]);
+    if (S[6]) return fail(PILOT_ECUDA, "%d out-of-range graph indices were skipped (checked build)", S[6]);
     if (S[0]) return fail(PILOT_EINVAL, "%d queries hold NaN or infinity (their results are -1 / +inf)", S[0]);
     return PILOT_OK;
 }

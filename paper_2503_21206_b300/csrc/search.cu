@@ -87,7 +87,27 @@ struct Warp {
     uint64_t* bar;      // mbarrier of this warp's row gathers
     uint32_t phase;     // parity of the barrier phase being waited for
     bool failed;        // a gather did not complete within kMaxPolls polls
+#ifdef PILOT_CHECKED
+    int32_t* status;    // status words: [6] counts out-of-range indices skipped (checked build)
+#endif
 };
+
+// Checked builds (-DPILOT_CHECKED) test every index read from the graph
+// before it addresses a row; an out-of-range index is counted in status
+// word 6 and skipped instead of being dereferenced.
+#ifdef PILOT_CHECKED
+#define PILOT_CHECK_INDEX(w, v, limit)                                        \
+    do {                                                                     \
+        if ((v) >= (limit)) {                                                \
+            if ((w).status) atomicAdd(&(w).status[6], 1);                    \
+            (v) = -1;                                                        \
+        }                                                                    \
+    } while (0)
+#else
+#define PILOT_CHECK_INDEX(w, v, limit) \
+    do {                               \
+    } while (0)
+#endif
 
 // Exact accumulation of one 16-byte chunk of a row into acc: the chunk holds
 // 4 FP32, 8 BF16 or 16 FP8 elements; qc points at the matching query elements;
@@ -517,7 +537,9 @@ struct Searcher {
         for (int b0 = 0; b0 < W; b0 += 32) {
             const int j = b0 + lane;
             int32_t v = j < W ? __ldg(row + j) : -1;
+            PILOT_CHECK_INDEX(w, v, view == 3 ? ix.n : ix.n_sub);
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
+            PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
             const unsigned vb = __ballot_sync(kFull, v >= 0);
             const int m = __popc(vb);
             if (m == 0) continue;
@@ -650,19 +672,57 @@ struct Searcher {
             int32_t orig = -1;
             if (lane < m) {
                 orig = __ldg(ix.sub2full + key_id(w.pool[b0 + lane]));
-                w.cand[lane] = orig;
+                PILOT_CHECK_INDEX(w, orig, ix.n);
+                w.cand[lane] = orig < 0 ? 0 : orig;
             }
             __syncwarp();
             full_batch(m);
             __syncwarp();
             if (lane < m) {
                 w.pool[b0 + lane] = make_key(w.dist[lane], orig);
-                w.stamps[orig] = uint8_t(w.epoch);
+                if (orig >= 0) w.stamps[orig] = uint8_t(w.epoch);
             }
             __syncwarp();
         }
         sort_pool(w, 0x7FFFFFFF);
         w.lb = 0;
+    }
+
+    // Explicit seeds for the final stage alone (stages (1)(2) off): C starts
+    // as the given distinct original ids (-1 entries skipped) with full
+    // distances, all unchecked and visited, the best ef kept.
+    __device__ void seed_start(QState& st, const int32_t* seeds, int count) {
+        const int lane = w.lane;
+        new_visited_set(w, ix.stamp_stride);
+        w.S = 0;
+        w.lb = 0;
+        int scored = 0;
+        for (int b0 = 0; b0 < count; b0 += kCand) {
+            const int j = b0 + lane;
+            const int32_t v = j < count ? seeds[j] : -1;
+            const unsigned vb = __ballot_sync(kFull, v >= 0);
+            const int m = __popc(vb);
+            if (m == 0) continue;
+            if (v >= 0) w.cand[__popc(vb & lanemask_lt())] = v;
+            __syncwarp();
+            full_batch(m);
+            __syncwarp();
+            uint64_t k = kKeyEmpty;
+            if (lane < m) {
+                k = make_key(w.dist[lane], w.cand[lane]);
+                w.stamps[w.cand[lane]] = uint8_t(w.epoch);
+            }
+            scored += m;
+            k = warp_sort32(k, lane);
+            merge_new(w, k, m, w.ef);
+            __syncwarp();
+        }
+        st.n_rerank = scored;
+        st.best = kKeyEmpty;
+        st.phase = kStage3;
+        st.it = 0;
+        w.lb = 0;
+        __syncwarp();
     }
 
     // Run the staged search from its current phase for at most `budget`
@@ -725,7 +785,7 @@ struct Searcher {
         if (w.lane == 0 && counters) {
             counters[0] = st.e1; counters[1] = st.d1; counters[2] = st.e2; counters[3] = st.d2;
             counters[4] = st.e3; counters[5] = st.d3; counters[6] = st.n_rerank;
-            counters[7] = __ldg(ix.sub2full + key_id(st.best));
+            counters[7] = st.best == kKeyEmpty ? -1 : __ldg(ix.sub2full + key_id(st.best));
         }
     }
 
@@ -733,7 +793,8 @@ struct Searcher {
         load_query(io.q_pad + q * ix.d_pad, io.qp + q * ix.qp_pad);
         QState st{};
         w.ef = cfg.ef;
-        fes(st, io.fes_pos + q * cfg.fes_T, io.fes_lb[q]);
+        if (io.seed_ids) seed_start(st, io.seed_ids + q * io.seed_count, io.seed_count);
+        else fes(st, io.fes_pos + q * cfg.fes_T, io.fes_lb[q]);
         advance(st, 0x7FFFFFFF);
         write_output(st, cfg.k, io.out_ids + q * cfg.k, io.out_dists + q * cfg.k,
                      io.counters ? io.counters + q * 8 : nullptr);
@@ -776,6 +837,9 @@ template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig cfg, SearchIO io, Layout L) {
     extern __shared__ __align__(128) uint8_t smem[];
     Warp w = setup_warp(L, smem);
+#ifdef PILOT_CHECKED
+    w.status = io.status;
+#endif
     const int slot = blockIdx.x * cfg.warps_per_block + (threadIdx.x >> 5);   // < ix.stamp_slots (launch bound)
     w.stamps = ix.stamps + int64_t(slot) * ix.stamp_stride;
     w.epoch_ctr = ix.stamp_epoch[slot];
@@ -811,6 +875,9 @@ template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConfig cfg, ServeIO sio, Layout L) {
     extern __shared__ __align__(128) uint8_t smem[];
     Warp w = setup_warp(L, smem);
+#ifdef PILOT_CHECKED
+    w.status = nullptr;
+#endif
     Searcher<DT, METRIC> s{ix, cfg, w};
     const int n_active = *reinterpret_cast<const volatile int32_t*>(sio.n_active);
     for (;;) {

@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpilot.so")
+# PILOT_LIBRARY selects another build of the same library (e.g. the checked one)
+LIB_PATH = os.environ.get("PILOT_LIBRARY") or os.path.join(_HERE, "libpilot.so")
 
 PILOT_OK, PILOT_EINVAL, PILOT_ENOMEM, PILOT_ECUDA, PILOT_EIO, PILOT_ETIMEOUT, PILOT_EBUSY, PILOT_EFORMAT = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EIO", "ETIMEOUT", "EBUSY", "EFORMAT"]
@@ -45,7 +46,7 @@ class pilot_search_options(ctypes.Structure):
     _fields_ = [("stage1", ctypes.c_int32), ("stage2_expansions", ctypes.c_int32), ("stage3", ctypes.c_int32),
                 ("use_fes", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("stage_rows", ctypes.c_int32),
                 ("counters", ctypes.c_void_p), ("kernel_ms", ctypes.c_void_p), ("status_words", ctypes.c_void_p),
-                ("fes_seeds", ctypes.c_int32)]
+                ("fes_seeds", ctypes.c_int32), ("seed_ids", ctypes.c_void_p), ("seed_count", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -287,6 +287,63 @@ def test_fes_seeds_out_of_range(c1, pilot, torch_cuda):
             gpu_search(pilot, torch_cuda, g, Q[:4], 10, 64, fes_seeds=bad)
 
 
+def _tau_seeds(gt, n, ef, tau, seed):
+    """tau true neighbours plus ef - tau distinct random other nodes per row."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for t in gt:
+        known = t[:tau].tolist()
+        pool = rng.permutation(n)
+        rest = [int(v) for v in pool[: ef + tau] if int(v) not in set(known)][: ef - tau]
+        rows.append(known + rest)
+    return np.asarray(rows, np.int32)
+
+
+@pytest.mark.parametrize("tau", [0, 8, 16])
+def test_seeded_final_stage_parity(c1, pilot, torch_cuda, tau):
+    """Sec. 4.2's experiment through the C ABI: the final stage alone from tau
+    known neighbours plus random nodes equals the oracle's run."""
+    w, idx, Q, _, g = c1
+    ef = 64
+    gt, _ = oracle.bruteforce(idx.full, Q, ef)
+    seeds = _tau_seeds(gt, idx.n, ef, tau, 3)
+    seeds[::7, -1] = -1                                   # skipped entries
+    ref = oracle.search(oracle_index(idx), Q, 10, ef, seed_ids=seeds)
+    o = pilot.pilot_search_options_default()
+    o.stage1, o.stage2_expansions = 0, 0
+    o.seed_ids, o.seed_count = seeds.ctypes.data, seeds.shape[1]
+    cnt = np.empty((len(Q), 8), np.int32)
+    ids, dists = pilot.pilot_search_ex(g, Q, 10, ef, options=o, counters=cnt)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+def test_seed_ids_validation(c1, pilot, torch_cuda):
+    w, idx, Q, _, g = c1
+    good = np.tile(np.arange(8, dtype=np.int32), (4, 1))
+
+    def run(seeds, **kw):
+        o = pilot.pilot_search_options_default()
+        o.stage1, o.stage2_expansions = 0, 0
+        for key, v in kw.items():
+            setattr(o, key, v)
+        o.seed_ids, o.seed_count = seeds.ctypes.data, seeds.shape[1]
+        return pilot.pilot_search_ex(g, Q[:4], 10, 16, options=o)
+
+    run(good)
+    for bad in (dict(stage1=1), dict(stage3=0), dict(stage2_expansions=2)):
+        with pytest.raises(pilot.PilotError):
+            run(good, **bad)
+    rep = good.copy()
+    rep[1, 3] = rep[1, 2]
+    out = good.copy()
+    out[2, 0] = idx.n
+    wide = np.tile(np.arange(17, dtype=np.int32), (4, 1))
+    for seeds in (rep, out, wide):
+        with pytest.raises(pilot.PilotError):
+            run(seeds)
+
+
 def test_load_from_files(c1, pilot, torch_cuda, tmp_path):
     w, idx, Q, _, g = c1
     index_build.save_index(idx, str(tmp_path))

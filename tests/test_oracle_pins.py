@@ -232,6 +232,32 @@ def test_fes_seeds_are_the_best_entries(c1_small, T, use_fes):
     assert np.all(r["counters"][:, 6] == np.minimum(64, r["counters"][:, 1] + T))
 
 
+def test_seeded_final_stage_hand_trace():
+    """Sec. 4.2's experiment on the path graph: the final stage alone, seeded
+    with given nodes (tests/golden/seeded_path_line.json)."""
+    line = json.load(open(os.path.join(GOLDEN, "alg1_path_line.json")))
+    g = json.load(open(os.path.join(GOLDEN, "seeded_path_line.json")))
+    ix = _plain_index(line["points"], line["graph"], line["entry"])
+    r = oracle.search(ix, np.asarray([line["query"]], np.float32), g["k"], g["ef"],
+                      seed_ids=np.asarray([g["seeds"]], np.int32))
+    assert r["ids"][0].tolist() == g["ids"]
+    np.testing.assert_array_equal(r["dists"][0], np.asarray(g["dists"], np.float32))
+    assert r["counters"][0].tolist() == g["counters"]
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_seeding_with_every_node_is_exact(metric):
+    """Seeds = every node (ef >= N): each seed is scored once, no expansion
+    finds an unvisited node, and the result is the exact top-k."""
+    ix, X, rng = _exact_limit_index(40, 8, 6, 31, metric=metric, unit=(metric == 1))
+    Q = rng.standard_normal((10, 8)).astype(np.float32)
+    seeds = np.tile(rng.permutation(40).astype(np.int32), (len(Q), 1))
+    r = oracle.search(ix, Q, 5, 40, seed_ids=seeds)
+    gt, gd = oracle.bruteforce(X, Q, 5, metric=metric)
+    assert np.array_equal(r["ids"], gt)
+    assert np.all(r["counters"][:, 5] == 0) and np.all(r["counters"][:, 6] == 40)
+
+
 def test_graceful_degradation(c1_small):
     """Sec. 4.1 'Summary': with stages (1) and (2) off, the search is plain
     greedy search over the full graph from the FES entry.  With ef >= reach
