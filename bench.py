@@ -477,6 +477,81 @@ def run_serve_sweep(args):
     return 0
 
 
+def run_sweep_sub(args):
+    """The GPU-piloting sensitivity of the paper's appendix (sampling ratio x
+    SVD ratio d'/d) on synthetic data: for each pair, the staged search's
+    smallest swept ef reaching recall@10 >= 0.95 and its batch QPS, beside
+    the plain final-stage form.  The full graph, the queries and the ground
+    truth are the workload's; only the subgraph (sample, re-built graph,
+    entries) and the reduced rows change per cell."""
+    import torch
+    from paper_2503_21206_b300 import index_build, pilot
+    from paper_2503_21206_b300.index_build import PilotIndexData
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq)
+    X, n, d = idx.full, idx.n, idx.d
+    nq, k = len(Q), w.k
+    V = index_build.svd_basis(X, w.graph_seed)
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    kms = np.zeros(3, np.float32)
+    efs = list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
+
+    def operating_point(g, opts):
+        ef_hit, rec = None, 0.0
+        for ef in efs:
+            pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=opts, kernel_ms=kms)
+            torch.cuda.synchronize()
+            rec = recall_at_k(ids.cpu().numpy(), gt, k)
+            ef_hit = ef
+            if rec >= 0.95:
+                break
+        step_ms, _ = timed_steps(lambda: pilot.pilot_search_ex(g, qd, k, ef_hit, ids, dists, stream,
+                                                               options=opts, kernel_ms=kms),
+                                 stream, flush, args.steps, args.warmup, kms)
+        return {"ef": ef_hit, "recall@10": round(rec, 5), "qps": nq / (step_ms / 1000.0)}
+
+    g = pilot.load_index_data(idx)
+    plain = pilot.pilot_search_options_default()
+    plain.stage1, plain.stage2_expansions = 0, 0
+    base_plain = operating_point(g, plain)
+    g.free()
+    cells = []
+    for sr in [float(x) for x in args.sample_ratios.split(",")]:
+        rng = np.random.default_rng(w.graph_seed)
+        n_sub = max(1, int(round(sr * n)))
+        sampled = np.sort(rng.choice(n, size=n_sub, replace=False)).astype(np.int64)
+        erng = np.random.default_rng(w.entry_seed)
+        n_entry = min(w.n_entry, n_sub)
+        entry_local = np.sort(erng.choice(n_sub, size=n_entry, replace=False))
+        sub_local = index_build.build_graph(X[sampled], w.R_sub, entry_local, device="cuda")
+        subgraph = np.full((n, w.R_sub), -1, np.int32)
+        subgraph[sampled] = np.where(sub_local >= 0, sampled[np.maximum(sub_local, 0)], -1).astype(np.int32)
+        mask = np.zeros(n, np.uint8)
+        mask[sampled] = 1
+        for svd_ratio in [float(x) for x in args.svd_ratios.split(",")]:
+            dp = max(1, int(round(svd_ratio * d)))
+            basis = np.ascontiguousarray(V[:, :dp])
+            red = index_build.project_rows(X[sampled], basis)
+            cell_idx = PilotIndexData(idx.graph, mask, subgraph, basis, red, "f32", None, X,
+                                      sampled[entry_local].astype(np.int32), idx.metric)
+            g = pilot.load_index_data(cell_idx)
+            op = operating_point(g, pilot.pilot_search_options_default())
+            g.free()
+            op.update({"sample_ratio": sr, "svd_ratio": svd_ratio, "dp": dp,
+                       "qps_vs_plain": round(op["qps"] / base_plain["qps"], 3)})
+            cells.append(op)
+            print(json.dumps(op), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "QPS@recall10=0.95 by sampling ratio x SVD ratio", "workload": args.workload,
+                      "n": n, "d": d, "nq": nq, "plain_final_stage": base_plain, "cells": cells,
+                      "data": "synthetic"}), flush=True)
+    return 0
+
+
 def run_tau(args):
     """The analysis of Sec. 4.2 (its tau/ef figures) on synthetic data: the
     final stage alone (Algorithm 1 on the full graph with full vectors),
@@ -782,6 +857,10 @@ def main(argv=None):
     ap.add_argument("--serve-sweep", action="store_true",
                     help="serving at each of --serve-rates (mixed k and ef) beside the batch operating points")
     ap.add_argument("--serve-rates", default="20000,50000,100000,200000")
+    ap.add_argument("--sweep-sub", action="store_true",
+                    help="sampling ratio x SVD ratio sweep of the staged search (QPS at recall 0.95)")
+    ap.add_argument("--sample-ratios", default="0.25,0.5,1.0")
+    ap.add_argument("--svd-ratios", default="0.25,0.5,1.0")
     ap.add_argument("--tau", action="store_true",
                     help="the tau/ef analysis: final stage seeded with tau true neighbours + random nodes")
     ap.add_argument("--ablation", action="store_true",
@@ -799,6 +878,8 @@ def main(argv=None):
         return run_serve_sweep(args)
     if args.tau:
         return run_tau(args)
+    if args.sweep_sub:
+        return run_sweep_sub(args)
     return run_forms(args) if args.forms else run_pilot(args)
 
 

@@ -207,8 +207,11 @@ def repair_reachability(X: np.ndarray, adj: np.ndarray, sources: np.ndarray, dev
     """Make every node reachable from ``sources`` (in place).
 
     Each round links every unreached node that no other unreached node points
-    to (or, if none, the unreached node closest to the reached set) from its
-    nearest reached node with a free adjacency slot.  Returns edges added."""
+    to (or, if none, the unreached node closest to the reached set -- one per
+    weakly connected group of unreached nodes when more than 16 such groups
+    remain, so that an index of many separate clusters does not take a round
+    per cluster) from its nearest reached node with a free adjacency slot.
+    Returns edges added."""
     dev = _dev(device)
     Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
     n, R = adj.shape
@@ -242,9 +245,25 @@ def repair_reachability(X: np.ndarray, adj: np.ndarray, sources: np.ndarray, dev
             best_i.append(i.cpu())
         bd = torch.cat(best_d).numpy()
         bi = F[torch.cat(best_i).numpy()]
-        if not S.size:   # only cycles remain: link the single closest node
-            j = int(np.argmin(bd[:, 0]))
-            pick, bd, bi = pick[j:j + 1], bd[j:j + 1], bi[j:j + 1]
+        if not S.size:   # only cycles remain: link the closest node (of each group, when many)
+            import scipy.sparse as sp
+            from scipy.sparse.csgraph import connected_components
+            pos = np.full(n, -1, np.int64)
+            pos[U] = np.arange(U.size)
+            src = np.repeat(np.arange(U.size), R)
+            dst = adj[U].reshape(-1)
+            ok = dst >= 0
+            ok[ok] = inU[dst[ok]]
+            sub = sp.csr_matrix((np.ones(int(ok.sum()), np.int8), (src[ok], pos[dst[ok]])),
+                                shape=(U.size, U.size))
+            n_comp, label = connected_components(sub, directed=True, connection="weak")
+            if n_comp <= 16:
+                js = [int(np.argmin(bd[:, 0]))]
+            else:
+                order = np.lexsort((bd[:, 0], label))          # by group, then distance
+                first = np.r_[True, label[order][1:] != label[order][:-1]]
+                js = order[first].tolist()
+            pick, bd, bi = pick[js], bd[js], bi[js]
         for u, cands in zip(pick, bi):
             placed = False
             for r in cands:
