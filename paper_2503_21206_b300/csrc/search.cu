@@ -528,10 +528,16 @@ struct Searcher {
         const int32_t* row = adjacency(view, u);
         const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
         // the next expansion most likely takes the second unchecked candidate:
-        // bring its adjacency row into L2 while this one is processed
-        if (idx2 >= 0 && lane == 0) {
+        // bring its adjacency row (every 128-byte line it spans) into L2 while
+        // this one is processed
+        if (idx2 >= 0) {
             const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
-            if (r2) asm volatile("prefetch.global.L2 [%0];" ::"l"(r2));
+            if (r2) {
+                const uintptr_t first = reinterpret_cast<uintptr_t>(r2) >> 7;
+                const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + (view == 3 ? ix.R : ix.R_sub)) - 1) >> 7;
+                if (uintptr_t(lane) <= last - first)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"((first + lane) << 7));
+            }
         }
         __syncwarp();
         for (int b0 = 0; b0 < W; b0 += 32) {
