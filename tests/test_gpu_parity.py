@@ -168,7 +168,7 @@ def test_argument_validation(c1, pilot, torch_cuda):
         assert e.value.status == pilot.PILOT_EINVAL
 
 
-@pytest.mark.parametrize("name", ["alg1_path_line.json", "alg1_local_minimum.json"])
+@pytest.mark.parametrize("name", ["alg1_path_line.json", "alg1_local_minimum.json", "alg1_two_cliques.json"])
 def test_golden_traces_on_gpu(pilot, torch_cuda, name):
     gdata = json.load(open(os.path.join(GOLDEN, name)))
     X = np.asarray(gdata["points"], np.float32)
@@ -181,6 +181,26 @@ def test_golden_traces_on_gpu(pilot, torch_cuda, name):
         assert ids[0].tolist() == case["ids"]
         np.testing.assert_array_equal(dists[0], np.asarray(case["dists"], np.float32))
         assert cnt[0, 4] == case["expansions"] and cnt[0, 5] == case["distances"]
+
+
+def test_seeded_golden_on_gpu(pilot, torch_cuda):
+    """The hand trace of the seeded final stage (tests/golden/seeded_path_line.json)."""
+    line = json.load(open(os.path.join(GOLDEN, "alg1_path_line.json")))
+    gd = json.load(open(os.path.join(GOLDEN, "seeded_path_line.json")))
+    X = np.asarray(line["points"], np.float32)
+    n, d = X.shape
+    G = np.asarray(line["graph"], np.int32)
+    g = pilot.pilot_index_load(G, np.ones(n, np.uint8), G, np.eye(d), X, X, np.asarray([line["entry"]], np.int32))
+    seeds = np.asarray([gd["seeds"]], np.int32)
+    o = pilot.pilot_search_options_default()
+    o.stage1, o.stage2_expansions = 0, 0
+    o.seed_ids, o.seed_count = seeds.ctypes.data, seeds.shape[1]
+    cnt = np.empty((1, 8), np.int32)
+    ids, dists = pilot.pilot_search_ex(g, np.asarray([line["query"]], np.float32), gd["k"], gd["ef"], options=o,
+                                       counters=cnt)
+    assert ids[0].tolist() == gd["ids"]
+    np.testing.assert_array_equal(dists[0], np.asarray(gd["dists"], np.float32))
+    assert cnt[0].tolist() == gd["counters"]
 
 
 def test_golden_staged_on_gpu(pilot, torch_cuda):

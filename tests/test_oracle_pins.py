@@ -27,7 +27,7 @@ def _plain_index(points, graph, entry, metric=0):
                               np.asarray([entry], np.int32), metric)
 
 
-@pytest.mark.parametrize("name", ["alg1_path_line.json", "alg1_local_minimum.json"])
+@pytest.mark.parametrize("name", ["alg1_path_line.json", "alg1_local_minimum.json", "alg1_two_cliques.json"])
 def test_algorithm1_hand_traces(name):
     g = json.load(open(os.path.join(GOLDEN, name)))
     ix = _plain_index(g["points"], g["graph"], g["entry"])
@@ -307,3 +307,42 @@ def test_recall_definition():
     found = np.asarray([[1, 2, 3], [4, 5, -1]])
     truth = np.asarray([[3, 2, 9], [5, 6, 7]])
     assert oracle.recall_at_k(found, truth, 3) == pytest.approx((2 + 1) / 6)
+
+
+try:
+    from hypothesis import given, settings, strategies as st
+except ImportError:   # pragma: no cover
+    given = None
+
+if given is not None:
+    @settings(max_examples=60, deadline=None)
+    @given(st.integers(2, 20), st.integers(1, 4), st.integers(1, 3), st.integers(0, 2**31 - 1))
+    def test_algorithm1_property_reachable_set(n, R, d, seed):
+        """Algorithm 1 with ef >= N on any small graph (Sec. 2.2): the result is
+        the brute-force top-k of the nodes reachable from the entry, every
+        reachable node is expanded once, and each one but the entry has its
+        distance computed once."""
+        rng = np.random.default_rng(seed)
+        X = rng.integers(-8, 9, size=(n, d)).astype(np.float32)   # small integers: exact FP32 distances
+        G = np.full((n, R), -1, np.int32)
+        for u in range(n):
+            nb = rng.choice(n, size=min(R, n), replace=False)
+            nb = nb[nb != u][: rng.integers(0, R + 1)]
+            G[u, : len(nb)] = nb
+        q = rng.integers(-8, 9, size=(1, d)).astype(np.float32)
+        ix = _plain_index(X, G, 0)
+        r = oracle.search(ix, q, min(3, n), n, stage1=False, stage2_expansions=0, use_fes=False)
+        seen, stack = {0}, [0]
+        while stack:
+            u = stack.pop()
+            for v in G[u]:
+                if v >= 0 and int(v) not in seen:
+                    seen.add(int(v))
+                    stack.append(int(v))
+        reach = np.asarray(sorted(seen))
+        dd = ((X[reach].astype(np.float64) - q[0]) ** 2).sum(1).astype(np.float32)
+        order = reach[np.lexsort((reach, dd))][: min(3, n)]
+        got = r["ids"][0][r["ids"][0] >= 0]
+        assert got.tolist() == order.tolist()
+        assert r["counters"][0, 4] == len(reach)
+        assert r["counters"][0, 5] == len(reach) - 1
