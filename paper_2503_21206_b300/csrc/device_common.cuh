@@ -113,17 +113,6 @@ __device__ __forceinline__ float df_finish(DF a, int metric) {
 
 __device__ __forceinline__ float bf16_to_f32(uint32_t h) { return __uint_as_float(h << 16); }
 
-// FP8 E4M3 "fn" code -> FP32 (exact): sign, 4-bit exponent with bias 7,
-// 3-bit mantissa, subnormals for a zero exponent field.  The NaN code is
-// rejected when an index is loaded.
-__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
-    uint32_t s = (c & 0x80u) << 24;
-    uint32_t e = (c >> 3) & 0xFu;
-    uint32_t m = c & 7u;
-    if (e == 0) return __uint_as_float(s | __float_as_uint(__uint2float_rn(m) * 0.001953125f));
-    return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
-}
-
 // Four E4M3 codes (one 32-bit word, first code in the low byte) -> FP32,
 // exactly, through the hardware pair conversion to FP16 (E4M3 is a subset).
 __device__ __forceinline__ void e4m3x4_to_f32(uint32_t wv, float (&x)[4]) {
@@ -224,17 +213,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
         if (done) return true;
     }
     return false;
-}
-
-// ------------------------------------------------------------- cp.async --
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 }  // namespace pilot

@@ -17,10 +17,11 @@
 // visited sets live in HBM: one byte per node for every warp slot, tagged with
 // a per-slot epoch so that a slot is cleared only once every 255 stages.  The
 // visited bytes of an expansion's neighbours are loaded together with their
-// rows, so the check adds no dependent memory round trip.  Distance batches: up to 32 rows;
-// eight lanes cover one 128-byte line of a row (16-byte cp.async copies into
-// shared memory), each lane owns 8 rows x its chunks, and a transposing
-// shuffle reduction leaves each row's sum in one lane.  New candidates are
+// rows, so the check adds no dependent memory round trip.  Distance batches: up to 32 rows,
+// each gathered into shared memory with one bulk copy completing on the warp's
+// mbarrier; eight lanes cover one 128-byte line of a row, each lane owns 8 rows
+// x its chunks, and a transposing shuffle reduction leaves each row's sum in
+// one lane.  New candidates are
 // sorted with a warp bitonic sort and merged into C by rank.
 #include <cfloat>
 
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int kCand = 32;   // distance batch (rows)
 constexpr int kMaxExpansionsPerStage = 1 << 22;
-constexpr bool kBoundedRejection = false;
 constexpr uint32_t kMaxPolls = 1u << 24;   // bound on polls of one gather's barrier
 
 struct Layout {
@@ -157,69 +157,6 @@ __device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, f
     }
 }
 
-// Plain FP32 sum of one chunk for the rejection test (a = sum (q - x)^2 for
-// L2; a = sum q x and b = sum |q| |x| for IP).
-template <int DT, int METRIC>
-__device__ __forceinline__ void approx_chunk(float& a, float& b, uint4 v, const float* qc, float sc) {
-    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        constexpr int PER = DT == 0 ? 1 : (DT == 1 ? 2 : 4);   // elements per 32-bit word
-        float x[PER], qe[PER];
-        if (DT == 0) {
-            x[0] = __uint_as_float(wv[h]);
-        } else if (DT == 1) {
-            x[0] = bf16_to_f32(wv[h] & 0xFFFFu);
-            x[PER - 1] = bf16_to_f32(wv[h] >> 16);
-        } else {
-            float c[4];
-            e4m3x4_to_f32(wv[h], c);
-#pragma unroll
-            for (int e = 0; e < PER; ++e) x[e] = c[e] * sc;
-        }
-        if (DT == 0) {
-            qe[0] = qc[h];
-        } else if (DT == 1) {
-            const float2 qv = *reinterpret_cast<const float2*>(qc + 2 * h);
-            qe[0] = qv.x;
-            qe[PER - 1] = qv.y;
-        } else {
-            const float4 qv = *reinterpret_cast<const float4*>(qc + 4 * h);
-            const float t[4] = {qv.x, qv.y, qv.z, qv.w};
-#pragma unroll
-            for (int e = 0; e < PER; ++e) qe[e] = t[e];
-        }
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            if (METRIC == 0) {
-                const float dd = qe[e] - x[e];
-                a = fmaf(dd, dd, a);
-            } else {
-                a = fmaf(qe[e], x[e], a);
-                b = fmaf(fabsf(qe[e]), fabsf(x[e]), b);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float reduce8f(float (&acc)[8], int mm) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = mm & 4;
-        const float send = up ? acc[i] : acc[i + 4];
-        acc[i] = (up ? acc[i + 4] : acc[i]) + __shfl_xor_sync(kFull, send, 4);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = mm & 2;
-        const float send = up ? acc[i] : acc[i + 2];
-        acc[i] = (up ? acc[i + 2] : acc[i]) + __shfl_xor_sync(kFull, send, 2);
-    }
-    const bool up = mm & 1;
-    const float send = up ? acc[0] : acc[1];
-    return (up ? acc[1] : acc[0]) + __shfl_xor_sync(kFull, send, 1);
-}
-
 // Transposing reduction over the eight lanes of a group: afterwards lane
 // (g, mm) holds the full sum of row slot g + 4 * mm.
 __device__ __forceinline__ DF reduce8(DF (&acc)[8], int mm) {
@@ -302,8 +239,8 @@ __device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__
 
 // Exact distances of rows cand[0..m) of a row array (`base`, `row_bytes` per
 // row, element type DT: 0 f32, 1 bf16, 2 fp8 codes with per-row `scales`) to
-// the query q in shared memory, into dist[0..m).  Rows are gathered with
-// 16-byte cp.async copies, P at a time (as many as the staging buffer holds).
+// the query q in shared memory, into dist[0..m).  Rows are gathered with one
+// bulk copy each, P at a time (as many as the staging buffer holds).
 template <int DT, int METRIC>
 __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
                                            const float* __restrict__ scales, const float* q, int m,
@@ -316,64 +253,6 @@ __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ 
         exact_staged<DT, METRIC>(w, row_bytes, scales, q, r1 - r0, [](int i) { return i; }, r0);
         __syncwarp();
     }
-}
-
-// Distances of rows cand[0..m) when the list is full and the next FP32 value
-// above its worst distance is reject_at.  Each row first gets a plain FP32 sum
-// with a rigorous rounding bound; a row whose lower bound reaches reject_at
-// has exact distance > the worst, so it cannot enter the list whatever the
-// ids, and is reported as +inf.  Only the remaining rows are computed exactly,
-// from the same staged data.  All m rows must fit in the staging buffer.  Not
-// used for FP8 rows with L2 (no simple relative bound for (q - fl(c s))^2).
-template <int DT, int METRIC>
-__device__ __forceinline__ void batch_dist_bounded(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
-                                                   const float* __restrict__ scales, const float* q, int m,
-                                                   float reject_at, int n_el) {
-    const int lane = w.lane, g = lane >> 3, mm = lane & 7;
-    const int F8 = row_bytes >> 7;
-    constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
-    gather_rows(w, base, row_bytes, 0, m);
-    const int jrows = (m + 3) >> 2;
-    float a[8], b[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        a[j] = 0.0f;
-        b[j] = 0.0f;
-        if (j < jrows) {
-            const int r = g + 4 * j < m ? g + 4 * j : 0;   // slots past m reread row 0
-            const uint8_t* rowp = w.stage + r * row_bytes;
-            const float sc = DT == 2 ? __ldg(scales + w.cand[r]) : 1.0f;
-            for (int t = 0; t < F8; ++t) {
-                const int c = mm + 8 * t;
-                approx_chunk<DT, METRIC>(a[j], b[j], *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
-            }
-        }
-    }
-    const float sa = reduce8f(a, mm);
-    const float sb = METRIC == 1 ? reduce8f(b, mm) : 0.0f;
-    // (n + 16) 2^-23 covers the relative error of an n-term FMA sum of
-    // non-negative terms (and, for IP, the dot product's error relative to
-    // sum |q| |x|) with a wide margin, including this line's own rounding.
-    const float eps = float(n_el + 16) * 1.1920929e-7f;
-    const float lbv = METRIC == 0 ? sa * (1.0f - eps) : (-sa - eps * sb * 1.001f);
-    const int r = g + 4 * mm;
-    const bool need = r < m && !(lbv >= reject_at);
-    if (r < m && !need) w.dist[r] = INFINITY;
-    const unsigned nb = __ballot_sync(kFull, need);
-    const int m2 = __popc(nb);
-    if (m2 == 0) return;
-    if (need) w.sel[__popc(nb & lanemask_lt())] = r;
-    __syncwarp();
-    exact_staged<DT, METRIC>(w, row_bytes, scales, q, m2, [&](int i) { return w.sel[i]; }, 0);
-}
-
-__device__ __forceinline__ uint64_t warp_min(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        uint64_t x = __shfl_xor_sync(kFull, v, o);
-        v = x < v ? x : v;
-    }
-    return v;
 }
 
 // Merge nb sorted new keys (lanes 0..nb-1, kKeyEmpty beyond) into C in place.
@@ -556,23 +435,10 @@ struct Searcher {
             // dropped afterwards
             const int32_t mine = lane < m ? w.cand[lane] : 0;
             const uint32_t tag = lane < m ? uint32_t(w.stamps[mine]) : w.epoch;
-            // once the list is full only rows that might enter it need exact
-            // distances (about one in ten late in a search)
-            const bool full_list = kBoundedRejection && w.S == w.ef;
-            const float reject_at = full_list ? nextafterf(key_dist(w.pool[w.S - 1]), INFINITY) : INFINITY;
-            if (view == 1) {
-                if (full_list && !(DT == 2 && METRIC == 0) && m * ix.red_row_bytes <= cfg.stage_bytes)
-                    batch_dist_bounded<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes,
-                                                   ix.red_scales, w.qp, m, reject_at, ix.dp_pad);
-                else
-                    reduced_batch(m);
-            } else {
-                if (full_list && m * ix.full_row_bytes <= cfg.stage_bytes)
-                    batch_dist_bounded<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes,
-                                                  nullptr, w.q, m, reject_at, ix.d_pad);
-                else
-                    full_batch(m);
-            }
+            if (view == 1)
+                reduced_batch(m);
+            else
+                full_batch(m);
             __syncwarp();
             const bool isnew = tag != w.epoch;
             if (isnew) w.stamps[mine] = uint8_t(w.epoch);
