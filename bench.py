@@ -685,7 +685,7 @@ def run_pilot(args):
     from paper_2503_21206_b300 import pilot
     w, idx, Q, gt = load_workload(args.workload, args.n, args.nq, verbose=(rank == 0))
     nq, k = len(Q), w.k
-    g = pilot.load_index_data(idx)
+    g = pilot.load_index_data(idx, full_vecs_host=args.full_host)
     stream = torch.cuda.Stream(device=device)
     qd = torch.from_numpy(Q).to(device)
     ids = torch.empty((nq, k), dtype=torch.int32, device=device)
@@ -815,6 +815,7 @@ def run_pilot(args):
                    "n_entry": int(len(idx.entry_ids)), "reduced_dtype": idx.reduced_dtype,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "sweep": sweep,
                    "parallelism": f"replicas x{ws}", "autotuned": tuned,
+                   "full_vecs": "pinned host memory" if args.full_host else "device",
                    "mean_counters": {name: round(float(c[:, i].mean()), 2) for i, name in
                                      enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(nq * idx.d * 4),
@@ -854,6 +855,8 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-budget", type=int, default=1024, help="expansions per request per step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--full-host", action="store_true",
+                    help="memory-bounded form: full vectors in pinned host memory, read over the host link")
     ap.add_argument("--serve-sweep", action="store_true",
                     help="serving at each of --serve-rates (mixed k and ef) beside the batch operating points")
     ap.add_argument("--serve-rates", default="20000,50000,100000,200000")

@@ -72,6 +72,15 @@ enum { PILOT_REDUCED_F32 = 0, PILOT_REDUCED_BF16 = 1, PILOT_REDUCED_FP8_E4M3 = 2
  *                  value = decode(code) * scale
  *  full_vecs       n x d float32 original vectors
  *  entry_ids       n_entry int32 FES entry set, each a sampled node
+ *  full_vecs_location
+ *                  where the library keeps its copy of the full vectors:
+ *                  PILOT_FULL_VECS_DEVICE (0, the default) in device memory,
+ *                  or PILOT_FULL_VECS_HOST (1) in pinned host memory mapped
+ *                  into the device's address space, for indexes whose full
+ *                  vectors do not fit beside the rest (the memory-bounded
+ *                  form: the GPU holds the subgraph, the reduced rows and the
+ *                  entries, and the re-rank and stages (2)(3) read full rows
+ *                  over the host link).  Results are identical either way.
  *
  * Rejected with PILOT_EINVAL: sizes out of range (n >= 2^31, R or R_sub above
  * PILOT_MAX_DEGREE, dp > d, n_entry < 1), an id outside [-1, n), a repeated id
@@ -90,7 +99,13 @@ typedef struct {
     const float* reduced_scales;
     const float* full_vecs;
     const int32_t* entry_ids;
+    int32_t full_vecs_location;     /* PILOT_FULL_VECS_* (0 = device) */
 } pilot_index_desc;
+
+#define PILOT_FULL_VECS_DEVICE 0
+#define PILOT_FULL_VECS_HOST 1
+/* pilot_index_load_files flag: keep the full vectors in pinned host memory */
+#define PILOT_LOAD_FULL_VECS_HOST 1
 
 /*
  * Copy an index to the current CUDA device.  *out receives the handle.  Besides
@@ -106,7 +121,9 @@ pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
  * "array <name> <i32|u8|u16|f32|f64> <bytes> <checksum hex>" line per array)
  * plus "<name>.bin" raw files.  The checksum is sum_i w_i * (2i + 1) mod 2^64
  * over the file's bytes as zero-padded little-endian 64-bit words w_i.
- * flags must be 0.  PILOT_EIO if a file is missing, PILOT_EFORMAT on a bad
+ * flags: 0 or PILOT_LOAD_FULL_VECS_HOST (full vectors in pinned host memory,
+ * as full_vecs_location = PILOT_FULL_VECS_HOST); PILOT_EINVAL for other
+ * bits.  PILOT_EIO if a file is missing, PILOT_EFORMAT on a bad
  * header, size or checksum; then the same validation as pilot_index_load.
  */
 pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** out);

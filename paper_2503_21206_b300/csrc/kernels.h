@@ -20,6 +20,7 @@ struct DevIndex {
     int full_row_bytes;  // d_pad * 4
     int red_row_bytes;   // dp_pad * element size
     int qp_pad;          // projected-query row length in floats (multiple of 64)
+    int full_host;       // 1: the full rows live in mapped pinned host memory (read with plain loads)
     const int32_t* graph;      // n x R original ids
     const int32_t* sub_adj;    // n_sub x R_sub compact ids
     const int32_t* sub2full;   // n_sub

@@ -73,10 +73,13 @@ struct pilot_index {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // per-kernel timing (on request)
     TunedShape tuned[kEfClasses] = {};   // autotuned search shapes by ef class
 
+    std::vector<void*> host_allocs;   // pinned, mapped (host-resident full vectors)
+
     ~pilot_index() {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
+        for (void* p : host_allocs) cudaFreeHost(p);
         if (ws) cudaFree(ws);
         if (status_host) cudaFreeHost(status_host);
     }
@@ -94,6 +97,23 @@ struct pilot_index {
     }
 
     // rows x width elements of esize bytes into rows x pitch_bytes, zero padded
+    // Rows copied into pinned host memory mapped into the device's address
+    // space; *out is the device-side address.
+    pilot_status map_rows(const void* host, int64_t rows, size_t width_bytes, size_t pitch_bytes, const void** out) {
+        void* h = nullptr;
+        size_t bytes = std::max<size_t>(size_t(rows) * pitch_bytes, 16);
+        CUDA_TRY(cudaHostAlloc(&h, bytes, cudaHostAllocMapped));
+        host_allocs.push_back(h);
+        std::memset(h, 0, bytes);
+        for (int64_t r = 0; r < rows; ++r)
+            std::memcpy(static_cast<char*>(h) + size_t(r) * pitch_bytes,
+                        static_cast<const char*>(host) + size_t(r) * width_bytes, width_bytes);
+        void* d = nullptr;
+        CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
+        *out = d;
+        return PILOT_OK;
+    }
+
     pilot_status upload_rows(const void* host, int64_t rows, size_t width_bytes, size_t pitch_bytes,
                              const void** out) {
         void* p = nullptr;
@@ -128,7 +148,7 @@ extern "C" {
 
 const char* pilot_last_error(void) { return g_error.c_str(); }
 
-int pilot_abi_version(void) { return 2; }
+int pilot_abi_version(void) { return 3; }
 
 void pilot_search_options_default(pilot_search_options* opt) {
     if (!opt) return;
@@ -185,6 +205,8 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     if (D.R < 1 || D.R > PILOT_MAX_DEGREE || D.R_sub < 1 || D.R_sub > PILOT_MAX_DEGREE)
         return fail(PILOT_EINVAL, "R and R_sub must be in [1, %d]", PILOT_MAX_DEGREE);
     if (D.n_entry < 1) return fail(PILOT_EINVAL, "n_entry must be >= 1");
+    if (D.full_vecs_location != PILOT_FULL_VECS_DEVICE && D.full_vecs_location != PILOT_FULL_VECS_HOST)
+        return fail(PILOT_EINVAL, "full_vecs_location must be PILOT_FULL_VECS_DEVICE or PILOT_FULL_VECS_HOST");
     if (D.metric != PILOT_METRIC_L2 && D.metric != PILOT_METRIC_IP) return fail(PILOT_EINVAL, "bad metric");
     if (D.reduced_dtype < 0 || D.reduced_dtype > 2) return fail(PILOT_EINVAL, "bad reduced_dtype");
     if (!D.graph || !D.subgraph_mask || !D.subgraph || !D.svd_basis || !D.reduced_vecs || !D.full_vecs ||
@@ -318,7 +340,12 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     if ((s = ix->upload_rows(D.reduced_vecs, n_sub, size_t(dp * esize), size_t(X.red_row_bytes), &p)) != PILOT_OK)
         return s;
     X.red = p;
-    if ((s = ix->upload_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) return s;
+    X.full_host = D.full_vecs_location == PILOT_FULL_VECS_HOST;
+    if (X.full_host) {
+        if ((s = ix->map_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) return s;
+    } else if ((s = ix->upload_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) {
+        return s;
+    }
     X.full = static_cast<const float*>(p);
     // visited bytes: one row of n bytes per warp slot, as many slots as the
     // search kernel can keep resident (16 warps per SM), within a quarter of
@@ -365,7 +392,7 @@ static uint64_t checksum64(const std::vector<char>& b) {
 
 pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** out) {
     if (!dir || !out) return fail(PILOT_EINVAL, "dir and out must not be NULL");
-    if (flags != 0) return fail(PILOT_EINVAL, "flags must be 0");
+    if (flags & ~PILOT_LOAD_FULL_VECS_HOST) return fail(PILOT_EINVAL, "unknown flags %d", flags);
     *out = nullptr;
     const std::string root(dir);
     std::ifstream hdr(root + "/pilot_index.txt");
@@ -433,6 +460,7 @@ pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** ou
     D.reduced_scales = dt == 2 ? reinterpret_cast<const float*>(arrays["reduced_scales"].data()) : nullptr;
     D.full_vecs = reinterpret_cast<const float*>(arrays["full"].data());
     D.entry_ids = reinterpret_cast<const int32_t*>(arrays["entry_ids"].data());
+    D.full_vecs_location = (flags & PILOT_LOAD_FULL_VECS_HOST) ? PILOT_FULL_VECS_HOST : PILOT_FULL_VECS_DEVICE;
     return pilot_index_load(&D, out);
 }
 

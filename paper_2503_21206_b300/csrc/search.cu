@@ -219,8 +219,24 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
 
 // Gather rows cand[r0..r1) (r1 - r0 <= 32) into the staging buffer: lane i
 // issues one bulk copy of row r0 + i; all complete on the warp's mbarrier.
-__device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int r0, int r1) {
+// Rows in host memory mapped into the device's address space (`plain`) are
+// copied instead with 16-byte loads spread over all lanes.
+__device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int r0, int r1,
+                                            bool plain) {
     const int n = r1 - r0;
+    if (plain) {
+        const int cpr = row_bytes >> 4;
+        const int total = n * cpr;
+        __syncwarp();
+#pragma unroll 4
+        for (int c = w.lane; c < total; c += 32) {
+            const int r = c / cpr, o = c - r * cpr;
+            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(w.cand[r0 + r]) * row_bytes + o * 16);
+            *reinterpret_cast<uint4*>(w.stage + r * row_bytes + o * 16) = v;
+        }
+        __syncwarp();
+        return;
+    }
     fence_proxy_async_smem();
     __syncwarp();
     if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
@@ -244,12 +260,12 @@ __device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__
 template <int DT, int METRIC>
 __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
                                            const float* __restrict__ scales, const float* q, int m,
-                                           int stage_bytes) {
+                                           int stage_bytes, bool plain) {
     int P = stage_bytes / row_bytes;
     P = P >= kCand ? kCand : (P & ~3);
     for (int r0 = 0; r0 < m; r0 += P) {
         const int r1 = r0 + P < m ? r0 + P : m;
-        gather_rows(w, base, row_bytes, r0, r1);
+        gather_rows(w, base, row_bytes, r0, r1, plain);
         exact_staged<DT, METRIC>(w, row_bytes, scales, q, r1 - r0, [](int i) { return i; }, r0);
         __syncwarp();
     }
@@ -360,11 +376,11 @@ struct Searcher {
 
     __device__ __forceinline__ void reduced_batch(int m) {
         batch_dist<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes, ix.red_scales, w.qp,
-                               m, cfg.stage_bytes);
+                               m, cfg.stage_bytes, false);
     }
     __device__ __forceinline__ void full_batch(int m) {
         batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr, w.q, m,
-                              cfg.stage_bytes);
+                              cfg.stage_bytes, ix.full_host != 0);
     }
 
     // Adjacency row of node u in a view (null if it has none).

@@ -19,6 +19,8 @@ LIB_PATH = os.environ.get("PILOT_LIBRARY") or os.path.join(_HERE, "libpilot.so")
 PILOT_OK, PILOT_EINVAL, PILOT_ENOMEM, PILOT_ECUDA, PILOT_EIO, PILOT_ETIMEOUT, PILOT_EBUSY, PILOT_EFORMAT = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EIO", "ETIMEOUT", "EBUSY", "EFORMAT"]
 METRIC_L2, METRIC_IP = 0, 1
+FULL_VECS_DEVICE, FULL_VECS_HOST = 0, 1
+LOAD_FULL_VECS_HOST = 1
 REDUCED_CODES = {"f32": 0, "bf16": 1, "fp8": 2}
 PILOT_MAX_EF = 512
 
@@ -39,7 +41,8 @@ class pilot_index_desc(ctypes.Structure):
                 ("R_sub", ctypes.c_int64), ("n_entry", ctypes.c_int64), ("metric", ctypes.c_int32),
                 ("reduced_dtype", ctypes.c_int32), ("graph", ctypes.c_void_p), ("subgraph_mask", ctypes.c_void_p),
                 ("subgraph", ctypes.c_void_p), ("svd_basis", ctypes.c_void_p), ("reduced_vecs", ctypes.c_void_p),
-                ("reduced_scales", ctypes.c_void_p), ("full_vecs", ctypes.c_void_p), ("entry_ids", ctypes.c_void_p)]
+                ("reduced_scales", ctypes.c_void_p), ("full_vecs", ctypes.c_void_p), ("entry_ids", ctypes.c_void_p),
+                ("full_vecs_location", ctypes.c_int32)]
 
 
 class pilot_search_options(ctypes.Structure):
@@ -124,8 +127,10 @@ class PilotIndex:
 
 
 def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, full_vecs, entry_ids, *,
-                     metric: int = METRIC_L2, reduced_dtype: str = "f32", reduced_scales=None) -> PilotIndex:
-    """Copy an index (host numpy arrays, layouts as in pilot.h) to the current device."""
+                     metric: int = METRIC_L2, reduced_dtype: str = "f32", reduced_scales=None,
+                     full_vecs_host: bool = False) -> PilotIndex:
+    """Copy an index (host numpy arrays, layouts as in pilot.h) to the current device.
+    ``full_vecs_host`` keeps the full vectors in pinned host memory instead."""
     arrs = dict(graph=np.ascontiguousarray(graph, np.int32), subgraph_mask=np.ascontiguousarray(subgraph_mask, np.uint8),
                 subgraph=np.ascontiguousarray(subgraph, np.int32),
                 svd_basis=np.ascontiguousarray(svd_basis, np.float64),
@@ -140,22 +145,23 @@ def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, fu
                             subgraph_mask=_addr(arrs["subgraph_mask"]), subgraph=_addr(arrs["subgraph"]),
                             svd_basis=_addr(arrs["svd_basis"]), reduced_vecs=_addr(arrs["reduced_vecs"]),
                             reduced_scales=_addr(sc), full_vecs=_addr(arrs["full_vecs"]),
-                            entry_ids=_addr(arrs["entry_ids"]))
+                            entry_ids=_addr(arrs["entry_ids"]),
+                            full_vecs_location=FULL_VECS_HOST if full_vecs_host else FULL_VECS_DEVICE)
     h = _P()
     _check(_lib.pilot_index_load(ctypes.byref(desc), ctypes.byref(h)))
     return PilotIndex(h.value)
 
 
-def load_index_data(idx) -> PilotIndex:
+def load_index_data(idx, full_vecs_host: bool = False) -> PilotIndex:
     """pilot_index_load of an ``index_build.PilotIndexData``."""
     return pilot_index_load(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, idx.full,
                             idx.entry_ids, metric=idx.metric, reduced_dtype=idx.reduced_dtype,
-                            reduced_scales=idx.reduced_scales)
+                            reduced_scales=idx.reduced_scales, full_vecs_host=full_vecs_host)
 
 
-def pilot_index_load_files(path: str) -> PilotIndex:
+def pilot_index_load_files(path: str, flags: int = 0) -> PilotIndex:
     h = _P()
-    _check(_lib.pilot_index_load_files(path.encode(), 0, ctypes.byref(h)))
+    _check(_lib.pilot_index_load_files(path.encode(), flags, ctypes.byref(h)))
     return PilotIndex(h.value)
 
 

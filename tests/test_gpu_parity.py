@@ -364,6 +364,34 @@ def test_seed_ids_validation(c1, pilot, torch_cuda):
             run(seeds)
 
 
+def test_full_vectors_in_host_memory(c1, pilot, torch_cuda, tmp_path):
+    """The memory-bounded form: full vectors in pinned host memory, read by the
+    re-rank and stages (2)(3) over the host link.  Results equal the oracle's
+    (and the device-resident index's), through both loaders, and through the
+    server."""
+    w, idx, Q, _, g_dev = c1
+    g = pilot.load_index_data(idx, full_vecs_host=True)
+    ref = oracle.search(oracle_index(idx), Q, 10, 64)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 64)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+    assert g.info()["device_bytes"] < g_dev.info()["device_bytes"]
+    index_build.save_index(idx, str(tmp_path))
+    g2 = pilot.pilot_index_load_files(str(tmp_path), pilot.LOAD_FULL_VECS_HOST)
+    ids2, dists2, _ = gpu_search(pilot, torch_cuda, g2, Q[:40], 10, 64)
+    assert np.array_equal(ids2, ref["ids"][:40]) and np.array_equal(dists2, ref["dists"][:40])
+    srv = pilot.pilot_serve_create(g, max_ef=64, max_k=10, expansions_per_step=16)
+    try:
+        tickets = [srv.submit(Q[i], 10, 64) for i in range(24)]
+        for i, t in enumerate(tickets):
+            sid, sd = srv.wait(t, 10)
+            assert np.array_equal(sid, ref["ids"][i]) and np.array_equal(sd, ref["dists"][i])
+    finally:
+        srv.destroy()
+    with pytest.raises(pilot.PilotError):
+        pilot.pilot_index_load_files(str(tmp_path), 2)
+
+
 def test_load_from_files(c1, pilot, torch_cuda, tmp_path):
     w, idx, Q, _, g = c1
     index_build.save_index(idx, str(tmp_path))
