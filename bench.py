@@ -646,6 +646,7 @@ def run_ablation(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     kms = np.zeros(3, np.float32)
     variants = [("staged (paper)", {}), ("fes_seeds=4", {"fes_seeds": 4}), ("fes_seeds=16", {"fes_seeds": 16}),
+                ("clustered FES (r = 32)", {"use_fes": 2}),
                 ("no FES (first entry)", {"use_fes": 0}), ("no stage (2) expansions", {"stage2_expansions": 0}),
                 ("no stage (1) (plain final stage)", {"stage1": 0, "stage2_expansions": 0})]
     rows = []

@@ -81,6 +81,12 @@ enum { PILOT_REDUCED_F32 = 0, PILOT_REDUCED_BF16 = 1, PILOT_REDUCED_FP8_E4M3 = 2
  *                  form: the GPU holds the subgraph, the reduced rows and the
  *                  entries, and the re-rank and stages (2)(3) read full rows
  *                  over the host link).  Results are identical either way.
+ *  n_clusters, entry_cluster, cluster_centroids
+ *                  optional coarse clusters of the entry set for the clustered
+ *                  FES of Sec. 5 (use_fes = 2): entry_cluster[n_entry] int32
+ *                  in [0, n_clusters), every cluster non-empty;
+ *                  cluster_centroids n_clusters x dp float32 in the reduced
+ *                  space.  n_clusters = 0 (and NULL arrays) when absent.
  *
  * Rejected with PILOT_EINVAL: sizes out of range (n >= 2^31, R or R_sub above
  * PILOT_MAX_DEGREE, dp > d, n_entry < 1), an id outside [-1, n), a repeated id
@@ -100,6 +106,9 @@ typedef struct {
     const float* full_vecs;
     const int32_t* entry_ids;
     int32_t full_vecs_location;     /* PILOT_FULL_VECS_* (0 = device) */
+    int64_t n_clusters;             /* entry clusters for the clustered FES, or 0 */
+    const int32_t* entry_cluster;
+    const float* cluster_centroids;
 } pilot_index_desc;
 
 #define PILOT_FULL_VECS_DEVICE 0
@@ -143,7 +152,11 @@ typedef struct {
     int32_t stage1;             /* 1: run stage (1) (default 1) */
     int32_t stage2_expansions;  /* stage (2) subgraph expansions (default 2, Sec. 4.1 (2)) */
     int32_t stage3;             /* 1: run stage (3) (default 1) */
-    int32_t use_fes;            /* 1: FES entry (default); 0: entry_ids[0] */
+    int32_t use_fes;            /* 1: dense FES over the entry set (default); 2: clustered FES
+                                   (Sec. 5): the query is routed to the cluster whose centroid
+                                   is closest by (reduced distance, cluster index) and only
+                                   that cluster's entries are scored (PILOT_EINVAL if the index
+                                   has no clusters); 0: the first entries of entry_ids */
     int32_t warps_per_block;    /* search warps (one query each) per block, 1..8; 0 = automatic
                                    (the autotuned shape of the ef class, else 2) */
     int32_t stage_rows;         /* rows of the widest kind gathered per pass into shared memory, 4..32

@@ -41,7 +41,8 @@ class _Index(ctypes.Structure):
                 ("subgraph", ctypes.c_void_p), ("basis", ctypes.c_void_p),
                 ("reduced", ctypes.c_void_p), ("reduced_dtype", ctypes.c_int),
                 ("reduced_scales", ctypes.c_void_p), ("full", ctypes.c_void_p),
-                ("entry_ids", ctypes.c_void_p)]
+                ("entry_ids", ctypes.c_void_p), ("n_clusters", ctypes.c_int64),
+                ("entry_cluster", ctypes.c_void_p), ("centroids", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -95,6 +96,8 @@ class OracleIndex:
     full: np.ndarray
     entry_ids: np.ndarray
     metric: int = METRIC_L2
+    entry_cluster: np.ndarray | None = None     # clustered FES: cluster of each entry
+    centroids: np.ndarray | None = None         # n_clusters x dp float32
 
     def _struct(self):
         arrs = dict(graph=np.ascontiguousarray(self.graph, np.int32),
@@ -105,13 +108,18 @@ class OracleIndex:
                     full=np.ascontiguousarray(self.full, np.float32),
                     entry_ids=np.ascontiguousarray(self.entry_ids, np.int32))
         scales = None if self.reduced_scales is None else np.ascontiguousarray(self.reduced_scales, np.float32)
+        if self.entry_cluster is not None:
+            arrs["entry_cluster"] = np.ascontiguousarray(self.entry_cluster, np.int32)
+            arrs["centroids"] = np.ascontiguousarray(self.centroids, np.float32)
         n, d = arrs["full"].shape
         s = _Index(n=n, d=d, dp=arrs["basis"].shape[1], R=arrs["graph"].shape[1],
                    R_sub=arrs["subgraph"].shape[1], n_entry=arrs["entry_ids"].shape[0],
                    metric=self.metric, graph=_ptr(arrs["graph"]), subgraph_mask=_ptr(arrs["subgraph_mask"]),
                    subgraph=_ptr(arrs["subgraph"]), basis=_ptr(arrs["basis"]), reduced=_ptr(arrs["reduced"]),
                    reduced_dtype=self.reduced_dtype, reduced_scales=_ptr(scales), full=_ptr(arrs["full"]),
-                   entry_ids=_ptr(arrs["entry_ids"]))
+                   entry_ids=_ptr(arrs["entry_ids"]),
+                   n_clusters=0 if self.centroids is None else int(np.asarray(self.centroids).shape[0]),
+                   entry_cluster=_ptr(arrs.get("entry_cluster")), centroids=_ptr(arrs.get("centroids")))
         return s, (arrs, scales)
 
 
@@ -120,7 +128,8 @@ def search(index: OracleIndex, queries: np.ndarray, k: int, ef: int, *, stage1: 
            nthreads: int = 1, pools: bool = False, seed_ids: np.ndarray | None = None) -> dict:
     """Staged PilotANN search (Sec. 4.1) of every query; returns a dict of arrays.
     ``fes_seeds`` entries (the best by reduced distance with FES, the first of
-    the entry set without) seed stage (1); the paper uses one.  ``seed_ids``
+    the entry set without) seed stage (1); the paper uses one.  ``use_fes=2``
+    is the clustered FES of Sec. 5 (needs the index's entry clusters).  ``seed_ids``
     (nq x T original ids, -1 skipped) instead seeds the final stage alone
     (the experiment of Sec. 4.2); the other stage options are then ignored."""
     lib = _load()

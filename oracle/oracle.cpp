@@ -44,6 +44,9 @@ struct Index {
     const float* reduced_scales;    // n_sub (FP8 only)
     const float* full;              // n x d FP32 original vectors
     const int32_t* entry_ids;       // n_entry original ids (all sampled)
+    int64_t n_clusters;             // clustered FES (Sec. 5): coarse clusters of the entry set, or 0
+    const int32_t* entry_cluster;   // n_entry cluster of each entry
+    const float* centroids;         // n_clusters x dp FP32 centroids in the reduced space
 };
 
 struct Params {
@@ -51,7 +54,7 @@ struct Params {
     int stage1;              // 1: run stage (1) on the subgraph (Sec. 4.1)
     int stage2_expansions;   // expansions of stage (2) on the subgraph (paper: 2)
     int stage3;              // 1: run stage (3) on the full graph
-    int use_fes;             // 1: dense FES over the entry set; 0: the first entries of entry_ids
+    int use_fes;             // 1: dense FES over the entry set; 2: clustered FES; 0: the first entries
     int fes_seeds;           // entries seeding stage (1) (the paper: 1)
     int nthreads;
     int seed_count;          // with seed_ids: entries per query row
@@ -159,6 +162,12 @@ struct Searcher {
         return finish(accumulate(qp, tmp, ix.dp, ix.metric), ix.metric);
     }
 
+    // Reduced-space distance from q' to coarse-cluster centroid c.
+    float centroid_dist(const double* qp, int64_t c, double* tmp) const {
+        for (int64_t i = 0; i < ix.dp; ++i) tmp[i] = double(ix.centroids[c * ix.dp + i]);
+        return finish(accumulate(qp, tmp, ix.dp, ix.metric), ix.metric);
+    }
+
     float full_dist(const double* q, int32_t v, double* tmp) const {
         const float* x = ix.full + int64_t(v) * ix.d;
         for (int64_t i = 0; i < ix.d; ++i) tmp[i] = double(x[i]);
@@ -222,12 +231,29 @@ void search_one(const Searcher& S, const Params& P, const float* query, int64_t 
     // paper seeds with the single closest one (fes_seeds = 1); more seeds are
     // the top-T variant.  Without FES the seeds are the first entries of the
     // set.  At most ef seeds.
-    const int64_t ns = std::min<int64_t>(std::min<int64_t>(P.fes_seeds, P.ef), ix.n_entry);
+    //
+    // Clustered FES (Sec. 5, "clustering-based selection"): the query goes to
+    // the coarse cluster whose centroid is closest by (distance, cluster
+    // index), and only that cluster's entries are scored.
     std::vector<Cand> seeds;
-    const int64_t n_scored = P.use_fes ? ix.n_entry : ns;
-    for (int64_t e = 0; e < n_scored; ++e)
-        seeds.push_back(Cand{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false});
+    if (P.use_fes == 2) {
+        int64_t best_c = 0;
+        float best_d = 0.0f;
+        for (int64_t c = 0; c < ix.n_clusters; ++c) {
+            const float dc = S.centroid_dist(qp.data(), c, tmp.data());
+            if (c == 0 || dc < best_d) { best_d = dc; best_c = c; }
+        }
+        for (int64_t e = 0; e < ix.n_entry; ++e)
+            if (ix.entry_cluster[e] == best_c)
+                seeds.push_back(Cand{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false});
+    } else {
+        const int64_t n_scored =
+            P.use_fes ? ix.n_entry : std::min<int64_t>(std::min<int64_t>(P.fes_seeds, P.ef), ix.n_entry);
+        for (int64_t e = 0; e < n_scored; ++e)
+            seeds.push_back(Cand{S.reduced_dist(qp.data(), ix.entry_ids[e], tmp.data()), ix.entry_ids[e], false});
+    }
     std::sort(seeds.begin(), seeds.end(), cand_less);
+    const int64_t ns = std::min<int64_t>(std::min<int64_t>(P.fes_seeds, P.ef), int64_t(seeds.size()));
     seeds.resize(size_t(ns));
     const Cand entry = seeds[0];
 
@@ -357,6 +383,16 @@ extern "C" {
 // Returns 0 on success, -1 on invalid arguments.
 int oracle_search(const Index* ix, const Params* P, const float* queries, int64_t nq, const Outputs* out) {
     if (!ix || !P || P->k < 1 || P->ef < P->k || ix->n_entry < 1 || P->fes_seeds < 1) return -1;
+    if (P->use_fes == 2) {   // every cluster must hold an entry
+        if (ix->n_clusters < 1 || !ix->entry_cluster || !ix->centroids) return -1;
+        std::vector<int64_t> size(size_t(ix->n_clusters), 0);
+        for (int64_t e = 0; e < ix->n_entry; ++e) {
+            if (ix->entry_cluster[e] < 0 || ix->entry_cluster[e] >= ix->n_clusters) return -1;
+            size[size_t(ix->entry_cluster[e])] += 1;
+        }
+        for (int64_t c : size)
+            if (c == 0) return -1;
+    }
     Searcher S(*ix);
     parallel_for(nq, P->nthreads, [&](int64_t qi) { search_one(S, *P, queries + qi * ix->d, qi, *out); });
     return 0;

@@ -85,7 +85,7 @@ extern "C" pilot_status pilot_autotune(pilot_index* index, const float* queries,
     }
     const std::string key = tune_key(*v.dev, v.device, cls) + "|s" + std::to_string(stages.stage1 != 0) + "." +
                             std::to_string(stages.stage2_expansions) + "." + std::to_string(stages.stage3 != 0) +
-                            "." + std::to_string(stages.use_fes != 0);
+                            "." + std::to_string(stages.use_fes);
     pilot_tune_result res{};
 
     if (cache_path) {

@@ -33,6 +33,13 @@ struct DevIndex {
     const float* entry_norm2;  // ||e||^2 (FP32 of the FP64 value), +inf past n_entry to whole 256-entry tiles
     float entry_max_norm;      // max ||e||
     const uint16_t* entry_bf16;   // entries as BF16, 256-row tiles in the UMMA K-major core-matrix layout
+    // clustered FES: centroid rows (n_clusters x cent_pad FP32, 128-byte rows),
+    // the entries' compact ids grouped by cluster, and each cluster's range
+    int n_clusters;
+    int cent_pad;
+    const float* centroids;
+    const int32_t* cl_entries;
+    const int32_t* cl_offsets;   // n_clusters + 1
     // Visited sets: one byte per node for each of stamp_slots warp slots (row
     // stride stamp_stride bytes); a node is visited in the current stage when
     // its byte equals the slot's current epoch.  stamp_epoch holds each slot's

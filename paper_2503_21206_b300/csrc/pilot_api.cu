@@ -148,7 +148,7 @@ extern "C" {
 
 const char* pilot_last_error(void) { return g_error.c_str(); }
 
-int pilot_abi_version(void) { return 3; }
+int pilot_abi_version(void) { return 4; }
 
 void pilot_search_options_default(pilot_search_options* opt) {
     if (!opt) return;
@@ -208,6 +208,22 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     if (D.full_vecs_location != PILOT_FULL_VECS_DEVICE && D.full_vecs_location != PILOT_FULL_VECS_HOST)
         return fail(PILOT_EINVAL, "full_vecs_location must be PILOT_FULL_VECS_DEVICE or PILOT_FULL_VECS_HOST");
     if (D.metric != PILOT_METRIC_L2 && D.metric != PILOT_METRIC_IP) return fail(PILOT_EINVAL, "bad metric");
+    if (D.n_clusters < 0 || D.n_clusters > D.n_entry)
+        return fail(PILOT_EINVAL, "n_clusters must be in [0, n_entry]");
+    if (D.n_clusters > 0) {
+        if (!D.entry_cluster || !D.cluster_centroids)
+            return fail(PILOT_EINVAL, "entry_cluster and cluster_centroids are required when n_clusters > 0");
+        std::vector<int64_t> size(size_t(D.n_clusters), 0);
+        for (int64_t e = 0; e < D.n_entry; ++e) {
+            if (D.entry_cluster[e] < 0 || D.entry_cluster[e] >= D.n_clusters)
+                return fail(PILOT_EINVAL, "entry_cluster[%lld] out of range", (long long)e);
+            size[size_t(D.entry_cluster[e])] += 1;
+        }
+        for (int64_t c = 0; c < D.n_clusters; ++c)
+            if (size[size_t(c)] == 0) return fail(PILOT_EINVAL, "cluster %lld has no entry", (long long)c);
+        for (int64_t i = 0; i < D.n_clusters * D.dp; ++i)
+            if (!std::isfinite(D.cluster_centroids[i])) return fail(PILOT_EINVAL, "a centroid is not finite");
+    }
     if (D.reduced_dtype < 0 || D.reduced_dtype > 2) return fail(PILOT_EINVAL, "bad reduced_dtype");
     if (!D.graph || !D.subgraph_mask || !D.subgraph || !D.svd_basis || !D.reduced_vecs || !D.full_vecs ||
         !D.entry_ids)
@@ -333,6 +349,22 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     entry_n2.resize(size_t(e_tiles * 256), INFINITY);   // whole tiles; padded entries never score
     if ((s = ix->upload(entry_n2.data(), entry_n2.size(), &X.entry_norm2)) != PILOT_OK) return s;
     if ((s = ix->upload(entry_bf16.data(), entry_bf16.size(), &X.entry_bf16)) != PILOT_OK) return s;
+    // clustered FES: FP32 centroid rows and the entries grouped by cluster
+    X.n_clusters = int(D.n_clusters);
+    X.cent_pad = round_up(int(dp), 32);
+    if (D.n_clusters > 0) {
+        std::vector<float> cent(size_t(D.n_clusters * X.cent_pad), 0.f);
+        for (int64_t c = 0; c < D.n_clusters; ++c)
+            for (int64_t k = 0; k < dp; ++k) cent[size_t(c * X.cent_pad + k)] = D.cluster_centroids[c * dp + k];
+        std::vector<int32_t> off(size_t(D.n_clusters + 1), 0), grouped(size_t(D.n_entry));
+        for (int64_t e = 0; e < D.n_entry; ++e) off[size_t(D.entry_cluster[e] + 1)] += 1;
+        for (int64_t c = 0; c < D.n_clusters; ++c) off[size_t(c + 1)] += off[size_t(c)];
+        std::vector<int32_t> fill(off.begin(), off.end() - 1);
+        for (int64_t e = 0; e < D.n_entry; ++e) grouped[size_t(fill[size_t(D.entry_cluster[e])]++)] = entry[size_t(e)];
+        if ((s = ix->upload(cent.data(), cent.size(), &X.centroids)) != PILOT_OK) return s;
+        if ((s = ix->upload(grouped.data(), grouped.size(), &X.cl_entries)) != PILOT_OK) return s;
+        if ((s = ix->upload(off.data(), off.size(), &X.cl_offsets)) != PILOT_OK) return s;
+    }
     X.red_scales = nullptr;
     if (D.reduced_dtype == 2)
         if ((s = ix->upload(D.reduced_scales, size_t(n_sub), &X.red_scales)) != PILOT_OK) return s;
@@ -461,6 +493,15 @@ pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** ou
     D.full_vecs = reinterpret_cast<const float*>(arrays["full"].data());
     D.entry_ids = reinterpret_cast<const int32_t*>(arrays["entry_ids"].data());
     D.full_vecs_location = (flags & PILOT_LOAD_FULL_VECS_HOST) ? PILOT_FULL_VECS_HOST : PILOT_FULL_VECS_DEVICE;
+    if (meta.count("n_clusters")) {   // optional entry clusters (clustered FES)
+        const int64_t nc = meta["n_clusters"];
+        if (!arrays.count("entry_cluster") || int64_t(arrays["entry_cluster"].size()) != ne * 4 ||
+            !arrays.count("cluster_centroids") || int64_t(arrays["cluster_centroids"].size()) != nc * dp * 4)
+            return fail(PILOT_EFORMAT, "missing or short entry_cluster / cluster_centroids");
+        D.n_clusters = nc;
+        D.entry_cluster = reinterpret_cast<const int32_t*>(arrays["entry_cluster"].data());
+        D.cluster_centroids = reinterpret_cast<const float*>(arrays["cluster_centroids"].data());
+    }
     return pilot_index_load(&D, out);
 }
 
@@ -522,7 +563,9 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     cfg.stage1 = opt.stage1 != 0;
     cfg.stage2_expansions = opt.stage2_expansions;
     cfg.stage3 = opt.stage3 != 0;
-    cfg.use_fes = opt.use_fes != 0;
+    if (opt.use_fes < 0 || opt.use_fes > 2) return fail(PILOT_EINVAL, "use_fes = %d outside [0, 2]", opt.use_fes);
+    if (opt.use_fes == 2 && X.n_clusters < 1) return fail(PILOT_EINVAL, "use_fes = 2 needs an index with entry clusters");
+    cfg.use_fes = opt.use_fes;
     cfg.fes_seeds = opt.fes_seeds;
     // explicit options first, then the autotuned shape of this ef class, then the defaults
     const TunedShape& tuned = ix->tuned[ef_class(ef)];
@@ -591,7 +634,7 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[0], st));
     CUDA_TRY(launch_project(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[1], st));
-    if (cfg.use_fes && !opt.seed_ids) CUDA_TRY(launch_fes_mma(X, io, st));
+    if (cfg.use_fes == 1 && !opt.seed_ids) CUDA_TRY(launch_fes_mma(X, io, st));
     if (timed) CUDA_TRY(cudaEventRecord(ix->ev[2], st));
     {
         cudaError_t e = launch_search(X, cfg, io, st, ix->num_sms);

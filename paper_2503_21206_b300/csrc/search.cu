@@ -343,6 +343,15 @@ __device__ __forceinline__ void sort_pool(Warp& w, int cap) {
     }
 }
 
+__device__ __forceinline__ uint64_t warp_min_key(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t x = __shfl_xor_sync(kFull, v, o);
+        v = x < v ? x : v;
+    }
+    return v;
+}
+
 enum Phase : int { kStage1 = 1, kRerank = 2, kStage2 = 3, kStage3 = 4, kDone = 5 };
 
 // Resumable per-query search state (the candidate list itself is in Warp).
@@ -478,12 +487,14 @@ struct Searcher {
         __syncwarp();
     }
 
-    // Fast entry selection (Sec. 5, dense form) seeding stage (1) with the
+    // Fast entry selection (Sec. 5) seeding stage (1) with the
     // best `ns` entries by (reduced distance, id): exact distances of the
     // scoring survivors, sorted; if the ns-th of them is not certified below
     // the bound on every other entry, an exact scan of the whole entry set
-    // keeps the best ns (merged into C with ef = ns).  Without FES the seeds
-    // are the first ns entries of the set.
+    // keeps the best ns (merged into C with ef = ns).  The clustered form
+    // (use_fes = 2) routes the query to the closest coarse cluster and scans
+    // only its entries the same way.  Without FES the seeds are the first ns
+    // entries of the set.
     __device__ void fes(QState& st, const int32_t* fes_pos, double fes_lb) {
         const int lane = w.lane;
         int ns = cfg.fes_seeds < w.ef ? cfg.fes_seeds : w.ef;
@@ -492,7 +503,7 @@ struct Searcher {
         w.S = 0;
         w.lb = 0;
         bool scan = false;
-        if (cfg.use_fes) {
+        if (cfg.use_fes == 1) {
             const int T = cfg.fes_T;
             const int32_t p = lane < T ? fes_pos[lane] : -1;
             const bool valid = p >= 0 && p < ix.n_entry;
@@ -510,7 +521,7 @@ struct Searcher {
             } else {
                 scan = true;
             }
-        } else {
+        } else if (cfg.use_fes == 0) {
             if (lane < ns) w.cand[lane] = __ldg(ix.entry + lane);
             __syncwarp();
             reduced_batch(ns);
@@ -519,13 +530,37 @@ struct Searcher {
             if (lane < ns) w.pool[lane] = key;
             w.S = ns;
         }
+        const int32_t* scan_list = ix.entry;   // entries scanned exactly, if any
+        int64_t scan_count = ix.n_entry;
+        if (cfg.use_fes == 2) {
+            // clustered FES (Sec. 5): route to the closest centroid by
+            // (reduced distance, cluster index), then scan that cluster
+            uint64_t bestc = kKeyEmpty;
+            for (int c0 = 0; c0 < ix.n_clusters; c0 += kCand) {
+                const int mm = ix.n_clusters - c0 < kCand ? ix.n_clusters - c0 : kCand;
+                if (lane < mm) w.cand[lane] = c0 + lane;
+                __syncwarp();
+                batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.centroids), ix.cent_pad * 4, nullptr,
+                                      w.qp, mm, cfg.stage_bytes, false);
+                __syncwarp();
+                const uint64_t k = warp_min_key(lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
+                bestc = k < bestc ? k : bestc;
+                __syncwarp();
+            }
+            const int c = int(key_id(bestc));
+            const int32_t lo = __ldg(ix.cl_offsets + c), hi = __ldg(ix.cl_offsets + c + 1);
+            scan_list = ix.cl_entries + lo;
+            scan_count = hi - lo;
+            if (ns > hi - lo) ns = hi - lo;
+            scan = true;
+        }
         if (scan) {
-            st.fallback = 1;
+            if (cfg.use_fes == 1) st.fallback = 1;
             const int ef_keep = w.ef;
             w.ef = ns;
-            for (int64_t e0 = 0; e0 < ix.n_entry; e0 += kCand) {
-                const int mm = ix.n_entry - e0 < kCand ? int(ix.n_entry - e0) : kCand;
-                if (lane < mm) w.cand[lane] = __ldg(ix.entry + e0 + lane);
+            for (int64_t e0 = 0; e0 < scan_count; e0 += kCand) {
+                const int mm = scan_count - e0 < kCand ? int(scan_count - e0) : kCand;
+                if (lane < mm) w.cand[lane] = __ldg(scan_list + e0 + lane);
                 __syncwarp();
                 reduced_batch(mm);
                 __syncwarp();

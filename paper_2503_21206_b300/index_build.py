@@ -45,6 +45,8 @@ class PilotIndexData:
     full: np.ndarray             # n x d float32
     entry_ids: np.ndarray        # n_entry int32
     metric: int                  # 0 L2, 1 IP
+    entry_cluster: np.ndarray | None = None       # n_entry int32: coarse cluster of each entry (clustered FES)
+    cluster_centroids: np.ndarray | None = None   # n_clusters x dp float32 centroids (reduced space)
 
     @property
     def n(self):
@@ -62,7 +64,7 @@ class PilotIndexData:
         """A copy whose reduced rows are ``reduced_f32`` stored as ``dtype``."""
         red, sc = quantize_rows(reduced_f32, dtype)
         return PilotIndexData(self.graph, self.subgraph_mask, self.subgraph, self.basis, red, dtype, sc,
-                              self.full, self.entry_ids, self.metric)
+                              self.full, self.entry_ids, self.metric, self.entry_cluster, self.cluster_centroids)
 
 
 # ------------------------------------------------------------------ kNN --
@@ -325,6 +327,47 @@ def quantize_rows(red: np.ndarray, dtype: str):
     raise ValueError(dtype)
 
 
+# -------------------------------------------------- entry clusters (Sec. 5) --
+
+def cluster_entries(E: np.ndarray, r: int, seed: int, iters: int = 8):
+    """Coarse, bucket-aligned clusters of the entry vectors for the clustered
+    FES of Sec. 5: r clusters of ceil(n / r) or fewer entries each.  Seeded
+    Lloyd iterations on the reduced FP32 rows, each assignment balanced by
+    taking (entry, centroid) pairs in order of distance while the centroid
+    has room; centroids are the FP64 means of their members rounded to FP32.
+    Returns (cluster of each entry int32, centroids r x dp float32)."""
+    E64 = np.asarray(E, np.float64)
+    n = E64.shape[0]
+    r = max(1, min(r, n))
+    rng = np.random.default_rng(seed)
+    C = E64[np.sort(rng.choice(n, size=r, replace=False))]
+    cap = -(-n // r)
+    assign = np.zeros(n, np.int64)
+    for _ in range(iters):
+        D = (E64 ** 2).sum(1)[:, None] - 2.0 * E64 @ C.T + (C ** 2).sum(1)[None, :]
+        order = np.argsort(D, axis=None, kind="stable")
+        room = np.full(r, cap)
+        assign[:] = -1
+        left = n
+        for flat in order:
+            e, c = divmod(int(flat), r)
+            if assign[e] < 0 and room[c] > 0:
+                assign[e] = c
+                room[c] -= 1
+                left -= 1
+                if left == 0:
+                    break
+        for c in range(r):
+            m = assign == c
+            if m.any():
+                C[c] = E64[m].mean(0)
+    # keep only non-empty clusters, renumbered in order
+    used = np.unique(assign)
+    remap = np.full(r, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    return remap[assign].astype(np.int32), C[used].astype(np.float32)
+
+
 # ------------------------------------------------------------ the index --
 
 def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int, n_entry: int, metric: int,
@@ -351,8 +394,10 @@ def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int,
     basis = np.ascontiguousarray(V[:, :dp])
     red32 = project_rows(X[sampled], basis)
     red, scales = quantize_rows(red32, reduced_dtype)
+    # coarse clusters of the entry set for the clustered FES (r = 32, Sec. 5)
+    ent_cluster, centroids = cluster_entries(red32[entry_local], 32, seed_entry)
     idx = PilotIndexData(graph, mask, subgraph, basis, red, reduced_dtype, scales,
-                         np.ascontiguousarray(X, np.float32), entry_ids, metric)
+                         np.ascontiguousarray(X, np.float32), entry_ids, metric, ent_cluster, centroids)
     if keep_reduced_f32:
         return idx, red32, V
     return idx
@@ -372,7 +417,8 @@ def build_workload(w: Workload, device=None, n: int | None = None, nq: int | Non
 # ------------------------------------------------------------ files --
 
 _FILES = [("graph", "i32"), ("subgraph_mask", "u8"), ("subgraph", "i32"), ("basis", "f64"),
-          ("reduced", None), ("reduced_scales", "f32"), ("full", "f32"), ("entry_ids", "i32")]
+          ("reduced", None), ("reduced_scales", "f32"), ("full", "f32"), ("entry_ids", "i32"),
+          ("entry_cluster", "i32"), ("cluster_centroids", "f32")]
 _NP = {"i32": np.int32, "u8": np.uint8, "f64": np.float64, "f32": np.float32, "u16": np.uint16}
 
 
@@ -396,6 +442,8 @@ def save_index(idx: PilotIndexData, path: str) -> None:
              f"R_sub {idx.subgraph.shape[1]}", f"n_sub {int(idx.subgraph_mask.sum())}",
              f"n_entry {idx.entry_ids.shape[0]}", f"metric {idx.metric}",
              f"reduced_dtype {DTYPE_CODES[idx.reduced_dtype]}"]
+    if idx.cluster_centroids is not None:
+        lines.append(f"n_clusters {idx.cluster_centroids.shape[0]}")
     for name, kind in _FILES:
         a = getattr(idx, name)
         if a is None:
@@ -427,7 +475,10 @@ def load_index(path: str) -> PilotIndexData:
     return PilotIndexData(arrays["graph"].reshape(n, meta["R"]), arrays["subgraph_mask"],
                           arrays["subgraph"].reshape(n, meta["R_sub"]), arrays["basis"].reshape(d, dp),
                           arrays["reduced"].reshape(meta["n_sub"], dp), rdt, arrays.get("reduced_scales"),
-                          arrays["full"].reshape(n, d), arrays["entry_ids"], meta["metric"])
+                          arrays["full"].reshape(n, d), arrays["entry_ids"], meta["metric"],
+                          arrays.get("entry_cluster"),
+                          arrays["cluster_centroids"].reshape(meta["n_clusters"], dp)
+                          if "cluster_centroids" in arrays else None)
 
 
 # ------------------------------------------------------ ground truth --

@@ -42,7 +42,8 @@ class pilot_index_desc(ctypes.Structure):
                 ("reduced_dtype", ctypes.c_int32), ("graph", ctypes.c_void_p), ("subgraph_mask", ctypes.c_void_p),
                 ("subgraph", ctypes.c_void_p), ("svd_basis", ctypes.c_void_p), ("reduced_vecs", ctypes.c_void_p),
                 ("reduced_scales", ctypes.c_void_p), ("full_vecs", ctypes.c_void_p), ("entry_ids", ctypes.c_void_p),
-                ("full_vecs_location", ctypes.c_int32)]
+                ("full_vecs_location", ctypes.c_int32), ("n_clusters", ctypes.c_int64),
+                ("entry_cluster", ctypes.c_void_p), ("cluster_centroids", ctypes.c_void_p)]
 
 
 class pilot_search_options(ctypes.Structure):
@@ -128,9 +129,10 @@ class PilotIndex:
 
 def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, full_vecs, entry_ids, *,
                      metric: int = METRIC_L2, reduced_dtype: str = "f32", reduced_scales=None,
-                     full_vecs_host: bool = False) -> PilotIndex:
+                     full_vecs_host: bool = False, entry_cluster=None, cluster_centroids=None) -> PilotIndex:
     """Copy an index (host numpy arrays, layouts as in pilot.h) to the current device.
-    ``full_vecs_host`` keeps the full vectors in pinned host memory instead."""
+    ``full_vecs_host`` keeps the full vectors in pinned host memory instead;
+    ``entry_cluster`` / ``cluster_centroids`` enable the clustered FES."""
     arrs = dict(graph=np.ascontiguousarray(graph, np.int32), subgraph_mask=np.ascontiguousarray(subgraph_mask, np.uint8),
                 subgraph=np.ascontiguousarray(subgraph, np.int32),
                 svd_basis=np.ascontiguousarray(svd_basis, np.float64),
@@ -138,6 +140,8 @@ def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, fu
                 full_vecs=np.ascontiguousarray(full_vecs, np.float32),
                 entry_ids=np.ascontiguousarray(entry_ids, np.int32))
     sc = None if reduced_scales is None else np.ascontiguousarray(reduced_scales, np.float32)
+    ec = None if entry_cluster is None else np.ascontiguousarray(entry_cluster, np.int32)
+    cc = None if cluster_centroids is None else np.ascontiguousarray(cluster_centroids, np.float32)
     n, d = arrs["full_vecs"].shape
     desc = pilot_index_desc(n=n, d=d, dp=arrs["svd_basis"].shape[1], R=arrs["graph"].shape[1],
                             R_sub=arrs["subgraph"].shape[1], n_entry=arrs["entry_ids"].shape[0], metric=metric,
@@ -146,7 +150,9 @@ def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, fu
                             svd_basis=_addr(arrs["svd_basis"]), reduced_vecs=_addr(arrs["reduced_vecs"]),
                             reduced_scales=_addr(sc), full_vecs=_addr(arrs["full_vecs"]),
                             entry_ids=_addr(arrs["entry_ids"]),
-                            full_vecs_location=FULL_VECS_HOST if full_vecs_host else FULL_VECS_DEVICE)
+                            full_vecs_location=FULL_VECS_HOST if full_vecs_host else FULL_VECS_DEVICE,
+                            n_clusters=0 if cc is None else cc.shape[0], entry_cluster=_addr(ec),
+                            cluster_centroids=_addr(cc))
     h = _P()
     _check(_lib.pilot_index_load(ctypes.byref(desc), ctypes.byref(h)))
     return PilotIndex(h.value)
@@ -156,7 +162,9 @@ def load_index_data(idx, full_vecs_host: bool = False) -> PilotIndex:
     """pilot_index_load of an ``index_build.PilotIndexData``."""
     return pilot_index_load(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, idx.full,
                             idx.entry_ids, metric=idx.metric, reduced_dtype=idx.reduced_dtype,
-                            reduced_scales=idx.reduced_scales, full_vecs_host=full_vecs_host)
+                            reduced_scales=idx.reduced_scales, full_vecs_host=full_vecs_host,
+                            entry_cluster=getattr(idx, "entry_cluster", None),
+                            cluster_centroids=getattr(idx, "cluster_centroids", None))
 
 
 def pilot_index_load_files(path: str, flags: int = 0) -> PilotIndex:

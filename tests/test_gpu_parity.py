@@ -36,7 +36,8 @@ def pilot(torch_cuda):
 def oracle_index(idx):
     dt = {"f32": oracle.DTYPE_F32, "bf16": oracle.DTYPE_BF16, "fp8": oracle.DTYPE_FP8}[idx.reduced_dtype]
     return oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, dt,
-                              idx.reduced_scales, idx.full, idx.entry_ids, idx.metric)
+                              idx.reduced_scales, idx.full, idx.entry_ids, idx.metric, idx.entry_cluster,
+                              idx.cluster_centroids)
 
 
 def gpu_search(pilot, torch, gidx, Q, k, ef, device=True, **opts):
@@ -390,6 +391,39 @@ def test_full_vectors_in_host_memory(c1, pilot, torch_cuda, tmp_path):
         srv.destroy()
     with pytest.raises(pilot.PilotError):
         pilot.pilot_index_load_files(str(tmp_path), 2)
+
+
+@pytest.mark.parametrize("T", [1, 4])
+def test_clustered_fes_parity(c1, pilot, torch_cuda, T):
+    """Clustered FES (Sec. 5, r = 32 coarse clusters): the GPU routes each
+    query to the same cluster and seeds stage (1) like the oracle."""
+    w, idx, Q, _, g = c1
+    assert idx.cluster_centroids is not None and idx.cluster_centroids.shape[0] == 32
+    ref = oracle.search(oracle_index(idx), Q, 10, 64, use_fes=2, fes_seeds=T)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 64, use_fes=2, fes_seeds=T)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+
+
+def test_clustered_fes_inner_product_files_and_errors(pilot, torch_cuda, tmp_path):
+    w = synth.WORKLOADS["c3_powerlaw_2m_d768"]
+    idx, Q, _, _ = index_build.build_workload(w, n=5000, nq=24, reduced_dtype="bf16")
+    index_build.save_index(idx, str(tmp_path))
+    g = pilot.pilot_index_load_files(str(tmp_path))
+    ref = oracle.search(oracle_index(idx), Q, 10, 48, use_fes=2, fes_seeds=2)
+    ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q, 10, 48, use_fes=2, fes_seeds=2)
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    assert np.array_equal(cnt, ref["counters"])
+    bare = pilot.pilot_index_load(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, idx.full,
+                                  idx.entry_ids, metric=idx.metric, reduced_dtype=idx.reduced_dtype)
+    with pytest.raises(pilot.PilotError):
+        gpu_search(pilot, torch_cuda, bare, Q[:4], 10, 48, use_fes=2)
+    bad = idx.entry_cluster.copy()
+    bad[bad == 3] = 4                                   # cluster 3 left empty
+    with pytest.raises(pilot.PilotError):
+        pilot.pilot_index_load(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, idx.full,
+                               idx.entry_ids, metric=idx.metric, reduced_dtype=idx.reduced_dtype,
+                               entry_cluster=bad, cluster_centroids=idx.cluster_centroids)
 
 
 def test_load_from_files(c1, pilot, torch_cuda, tmp_path):

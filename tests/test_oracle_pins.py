@@ -258,6 +258,51 @@ def test_seeding_with_every_node_is_exact(metric):
     assert np.all(r["counters"][:, 5] == 0) and np.all(r["counters"][:, 6] == 40)
 
 
+def _with_clusters(idx, entry_cluster, centroids):
+    return oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced, 0, None,
+                              idx.full, idx.entry_ids, 0, np.asarray(entry_cluster, np.int32),
+                              np.asarray(centroids, np.float32))
+
+
+def test_clustered_fes_special_cases_equal_dense_fes(c1_small):
+    """Sec. 5 / Table 2: with one cluster ('1 block') the clustered FES is the
+    dense one; with one entry per cluster and each centroid equal to its
+    entry's reduced row it again picks the dense argmin (entries are in
+    ascending id order, so cluster-index ties break like id ties)."""
+    idx, Q, red32, _ = c1_small
+    sub_ids = np.nonzero(idx.subgraph_mask)[0]
+    row_of = {int(v): i for i, v in enumerate(sub_ids)}
+    E = np.asarray([red32[row_of[int(e)]] for e in idx.entry_ids], np.float32)
+    dense = oracle.search(_with_clusters(idx, np.zeros(len(E)), E[:1]), Q, 10, 64, use_fes=True, fes_seeds=3)
+    one = oracle.search(_with_clusters(idx, np.zeros(len(E)), E[:1]), Q, 10, 64, use_fes=2, fes_seeds=3)
+    each = oracle.search(_with_clusters(idx, np.arange(len(E)), E), Q, 10, 64, use_fes=2)
+    ref1 = oracle.search(_with_clusters(idx, np.zeros(len(E)), E[:1]), Q, 10, 64, use_fes=True)
+    for a, b in ((one, dense), (each, ref1)):
+        assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["counters"], b["counters"])
+
+
+def test_clustered_fes_routes_then_takes_the_cluster_argmin(c1_small):
+    """The entry is the (distance, id) argmin over the entries of the cluster
+    whose centroid is closest to q' by (distance, cluster index)."""
+    idx, Q, red32, _ = c1_small
+    ix = _with_clusters(idx, idx.entry_cluster, idx.cluster_centroids)
+    r = oracle.search(ix, Q, 10, 64, stage1=False, stage2_expansions=0, stage3=False, use_fes=2, pools=True)
+    _, qp = oracle.project(ix, Q)
+    sub_ids = np.nonzero(idx.subgraph_mask)[0]
+    row_of = {int(v): i for i, v in enumerate(sub_ids)}
+    E = np.asarray([red32[row_of[int(e)]] for e in idx.entry_ids], np.float64)
+    C = idx.cluster_centroids.astype(np.float64)
+    assert np.bincount(idx.entry_cluster).max() - np.bincount(idx.entry_cluster).min() <= 1
+    for i in range(len(Q)):
+        q = qp[i].astype(np.float64)
+        dc = ((q - C) ** 2).sum(1).astype(np.float32)
+        c = int(np.lexsort((np.arange(len(C)), dc))[0])
+        members = np.nonzero(idx.entry_cluster == c)[0]
+        dd = ((q - E[members]) ** 2).sum(1).astype(np.float32)
+        j = members[np.lexsort((idx.entry_ids[members], dd))[0]]
+        assert r["pool1_ids"][i, 0] == idx.entry_ids[j]
+
+
 def test_graceful_degradation(c1_small):
     """Sec. 4.1 'Summary': with stages (1) and (2) off, the search is plain
     greedy search over the full graph from the FES entry.  With ef >= reach
