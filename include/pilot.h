@@ -130,6 +130,8 @@ pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
  * "array <name> <i32|u8|u16|f32|f64> <bytes> <checksum hex>" line per array)
  * plus "<name>.bin" raw files.  The checksum is sum_i w_i * (2i + 1) mod 2^64
  * over the file's bytes as zero-padded little-endian 64-bit words w_i.
+ * Optional: "n_clusters <r>" with arrays entry_cluster (i32, n_entry) and
+ * cluster_centroids (f32, r x dp) for the clustered FES.
  * flags: 0 or PILOT_LOAD_FULL_VECS_HOST (full vectors in pinned host memory,
  * as full_vecs_location = PILOT_FULL_VECS_HOST); PILOT_EINVAL for other
  * bits.  PILOT_EIO if a file is missing, PILOT_EFORMAT on a bad
