@@ -85,3 +85,30 @@ def test_workloads_are_seeded_and_prefix_stable():
         xa, qa = synth.generate(wl, n=300, nq=20)
         xb, qb = synth.generate(wl, n=900, nq=70)
         assert np.array_equal(xa, xb[:300]) and np.array_equal(qa, qb[:20])
+
+
+def test_entry_clusters_are_bucket_aligned_and_seeded():
+    """The clustered FES's coarse clusters (Sec. 5): non-empty clusters of at
+    most ceil(n / r) entries (exactly n / r each when r divides n), each
+    centroid the mean of its members, the same assignment for the same seed."""
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal((1000, 16)).astype(np.float32)
+    a1, c1 = index_build.cluster_entries(E, 32, 9)
+    a2, c2 = index_build.cluster_entries(E, 32, 9)
+    assert np.array_equal(a1, a2) and np.array_equal(c1, c2)
+    sizes = np.bincount(a1, minlength=32)
+    assert c1.shape == (32, 16) and sizes.min() >= 1 and sizes.max() <= 32
+    even, _ = index_build.cluster_entries(E[:992], 32, 9)
+    assert np.all(np.bincount(even, minlength=32) == 31)
+    for c in range(32):
+        np.testing.assert_allclose(c1[c], E[a1 == c].astype(np.float64).mean(0), rtol=1e-5, atol=1e-6)
+    a3, c3 = index_build.cluster_entries(E[:5], 32, 9)      # fewer entries than clusters: one each
+    assert sorted(a3.tolist()) == list(range(5)) and c3.shape == (5, 16)
+
+
+def test_save_load_keeps_entry_clusters(tmp_path, c1_small):
+    idx, _, _, _ = c1_small
+    index_build.save_index(idx, str(tmp_path))
+    back = index_build.load_index(str(tmp_path))
+    assert np.array_equal(back.entry_cluster, idx.entry_cluster)
+    assert np.array_equal(back.cluster_centroids, idx.cluster_centroids)
