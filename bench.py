@@ -535,6 +535,10 @@ def run_sweep_sub(args):
         mask[sampled] = 1
         for svd_ratio in [float(x) for x in args.svd_ratios.split(",")]:
             dp = max(1, int(round(svd_ratio * d)))
+            if dp > 128:   # the library keeps d' <= 128
+                cells.append({"sample_ratio": sr, "svd_ratio": svd_ratio, "dp": dp,
+                              "skipped": "d' above the library's limit of 128"})
+                continue
             basis = np.ascontiguousarray(V[:, :dp])
             red = index_build.project_rows(X[sampled], basis)
             cell_idx = PilotIndexData(idx.graph, mask, subgraph, basis, red, "f32", None, X,
