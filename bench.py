@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
 EXTRA_EFS = (384, 512)
+# the compact precision-form comparison of the default line
+FORMS_WORKLOAD, FORMS_N, FORMS_NQ = "c3_powerlaw_2m_d768", 200_000, 2_000
 
 
 # ----------------------------------------------------------- distributed --
@@ -182,7 +184,7 @@ def algorithmic_bytes(counters: np.ndarray, k: int, idx, T: int = 8) -> float:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("search.cu", "device_common.cuh"):
+    for f in ("search_impl.cuh", "device_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2503_21206_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -207,12 +209,13 @@ def oracle_index(idx):
                               idx.entry_ids, idx.metric)
 
 
-def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q: int = 4000):
-    """The oracle as it stands, on all host cores, over a bounded query sample.
-    Returns (qps, queries, seconds, threads)."""
+def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q: int = 4000, threads: int = 0):
+    """The oracle as it stands, on `threads` host threads (all cores by
+    default), over a bounded query sample.  Returns (qps, queries, seconds,
+    threads)."""
     import oracle
     oi = oracle_index(idx)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     n = min(min_q, len(Q))
     t0 = time.perf_counter()
     oracle.search(oi, Q[:n], k, ef, nthreads=threads)
@@ -223,6 +226,16 @@ def oracle_sample(idx, Q, k, ef, budget_s: float = 12.0, min_q: int = 64, max_q:
         oracle.search(oi, Q[:n], k, ef, nthreads=threads)
         dt = time.perf_counter() - t0
     return n / dt, n, dt, threads
+
+
+def cpu_baseline_entry(idx, Q, k, ef) -> dict:
+    """The oracle on all host cores (the reported value) and on one thread."""
+    qps, ns, secs, threads = oracle_sample(idx, Q, k, ef)
+    qps1, ns1, secs1, _ = oracle_sample(idx, Q, k, ef, budget_s=4.0, min_q=8, max_q=512, threads=1)
+    return {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {ns} of {len(Q)} queries, ef={ef}, {secs:.1f}s on {threads} host threads",
+            "value_1thread": qps1,
+            "sample_1thread": f"first {ns1} of {len(Q)} queries, ef={ef}, {secs1:.1f}s on 1 host thread"}
 
 
 # ------------------------------------------------------------------ arms --
@@ -350,20 +363,23 @@ def timed_steps(search, stream, flush, steps: int, warmup: int, kms):
     return statistics.mean(step_ms), statistics.mean(search_ms)
 
 
-def run_forms(args):
+def measure_forms(workload, n, nq, steps, warmup, serve_requests, serve_budget, autotune, fixed_ef=0,
+                  serving=True, dtypes=None, plain=True, log=True):
     """Precision forms of one workload on one GPU: reduced rows in FP32, BF16
-    and FP8-E4M3 (the workload's list), plus the plain form (only the final
-    stage: Algorithm 1 on the full graph with full rows, seeded by FES).  For
-    each, the smallest swept ef reaching recall@10 >= 0.95 against the FP64
-    brute force, batch QPS there, the search kernel's fraction of HBM peak, the
-    distance error against FP64, and a saturating serving run at that ef."""
+    and FP8-E4M3 (the workload's list, or `dtypes`), plus the plain form (only
+    the final stage: Algorithm 1 on the full graph with full rows, seeded by
+    FES).  For each, the smallest swept ef reaching recall@10 >= 0.95 against
+    the FP64 brute force, batch QPS there, the search kernel's fraction of HBM
+    peak, the distance error against FP64, and a saturating serving run at
+    that ef (offered at twice the batch rate).  Returns (index, list of
+    per-form records)."""
     import torch
     from paper_2503_21206_b300 import pilot
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
-    w, idx32, Q, gt = load_workload(args.workload, args.n, args.nq)
+    w, idx32, Q, gt = load_workload(workload, n, nq)
     if idx32.reduced_dtype != "f32":
-        raise SystemExit("--forms needs a workload whose index stores FP32 reduced rows")
+        raise SystemExit("the precision forms need a workload whose index stores FP32 reduced rows")
     red32 = idx32.reduced
     nq, k = len(Q), w.k
     stream = torch.cuda.Stream(device=device)
@@ -374,8 +390,10 @@ def run_forms(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     kms = np.zeros(3, np.float32)
     peak, peak_kind = measured_peaks()
-    efs = [args.ef] if args.ef else list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
-    forms = [(dt, dict()) for dt in w.reduced_dtypes] + [("f32", dict(stage1=0, stage2_expansions=0))]
+    efs = [fixed_ef] if fixed_ef else list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
+    forms = [(dt, dict()) for dt in (dtypes or w.reduced_dtypes)]
+    if plain:
+        forms.append(("f32", dict(stage1=0, stage2_expansions=0)))
     out = []
     for dt, sw in forms:
         idx = idx32 if dt == "f32" else idx32.with_reduced(dt, red32)
@@ -388,6 +406,8 @@ def run_forms(args):
             return pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, options=opts, counters=counters,
                                          kernel_ms=kms)
 
+        search(efs[0])   # untimed: module loading and the first workspace allocation
+        torch.cuda.synchronize()
         sweep, ef = [], None
         for cand in efs:
             search(cand)
@@ -397,13 +417,13 @@ def run_forms(args):
             ef = cand
             if rec >= 0.95:
                 break
-        tuned = None if args.no_autotune else pilot.pilot_autotune(g, qd, k, ef, stream, options=opts)
+        tuned = pilot.pilot_autotune(g, qd, k, ef, stream, options=opts) if autotune else None
         search(ef, cnt)
         torch.cuda.synchronize()
         counters = cnt.cpu().numpy()
         h_ids, h_d = ids.cpu().numpy(), dists.cpu().numpy()
         recall = recall_at_k(h_ids, gt, k)
-        step_ms, search_ms = timed_steps(lambda: search(ef), stream, flush, args.steps, args.warmup, kms)
+        step_ms, search_ms = timed_steps(lambda: search(ef), stream, flush, steps, warmup, kms)
         alg = algorithmic_bytes(counters, k, idx)
         c = counters.astype(np.float64)
         rec_form = {"form": "plain (final stage only)" if sw else "staged", "reduced_dtype": dt, "ef": ef,
@@ -414,20 +434,33 @@ def run_forms(args):
                     "autotuned": tuned,
                     "mean_counters": {name: round(float(c[:, i].mean()), 1) for i, name in
                                       enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}}
-        if not args.no_serving and not sw:   # the server always runs every stage
+        if serving and not sw:   # the server always runs every stage
             rate = 2.0 * rec_form["qps"]
-            rec_form["serving"] = serving_run(pilot, g, Q, gt, rate, min(args.serve_requests, int(rate * 4) + 1000),
+            rec_form["serving"] = serving_run(pilot, g, Q, gt, rate, min(serve_requests, int(rate * 4) + 1000),
                                               fixed_ef=ef, max_ef=512, max_k=100,
-                                              expansions_per_step=args.serve_budget)
+                                              expansions_per_step=serve_budget)
         out.append(rec_form)
-        print(json.dumps(rec_form), file=sys.stderr, flush=True)
+        if log:
+            print(json.dumps(rec_form), file=sys.stderr, flush=True)
         g.free()
         del g
+    return idx32, out
+
+
+def run_forms(args):
+    """The precision forms of --workload as one JSON line (see measure_forms)."""
+    idx32, out = measure_forms(args.workload, args.n, args.nq, args.steps, args.warmup, args.serve_requests,
+                               args.serve_budget, not args.no_autotune, fixed_ef=args.ef,
+                               serving=not args.no_serving)
+    peak, peak_kind = measured_peaks()
     base = next(f for f in out if f["form"] != "staged")
+    from paper_2503_21206_b300 import synth
+    w = synth.WORKLOADS[args.workload]
     line = {"metric": "QPS@recall10=0.95 by precision form", "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
-            "config": {"workload": args.workload, "n": idx32.n, "d": idx32.d, "dp": idx32.dp, "nq": nq, "k": k,
-                       "metric": "ip" if idx32.metric else "l2", "R": int(idx32.graph.shape[1]),
+            "config": {"workload": args.workload, "n": idx32.n, "d": idx32.d, "dp": idx32.dp,
+                       "nq": args.nq or w.nq, "k": w.k, "metric": "ip" if idx32.metric else "l2",
+                       "R": int(idx32.graph.shape[1]),
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
             "peak": {"hbm_gbs": peak, "source": peak_kind},
             "forms": out,
@@ -435,6 +468,32 @@ def run_forms(args):
                              round(f["qps"] / base["qps"], 3) for f in out}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def forms_summary(args) -> dict:
+    """The compact comparison in the default line: on the first FORMS_N rows
+    of the 768-d power-law workload (IP, d' = 128, where BF16 rows are half
+    the bytes of FP32 ones), the served BF16 staged form against the served
+    FP32 staged form and the plain FP32 form, each at its smallest ef reaching
+    recall@10 >= 0.95, measured in this run."""
+    idx32, out = measure_forms(FORMS_WORKLOAD, FORMS_N, FORMS_NQ, 3, 3, 30_000, args.serve_budget,
+                               autotune=False, dtypes=("f32", "bf16"), log=False)
+    by = {("plain" if f["form"] != "staged" else f["reduced_dtype"]): f for f in out}
+    brief = {}
+    for name, f in by.items():
+        e = {"ef": f["ef"], "recall@10": f["recall@10"], "batch_qps": round(f["qps"], 1),
+             "hbm_frac": round(f["hbm_frac"], 4)}
+        if "serving" in f:
+            e["served_qps"] = f["serving"]["qps"]
+            e["served_recall@min(k,10)"] = f["serving"]["recall@min(k,10)"]
+            e["served_p99_ms"] = f["serving"]["p99_ms"]
+        brief[name] = e
+    res = {"workload": f"{FORMS_WORKLOAD} first {idx32.n} rows, {FORMS_NQ} queries", "forms": brief}
+    if "served_qps" in brief.get("bf16", {}) and "served_qps" in brief.get("f32", {}):
+        res["served_bf16_over_served_f32"] = round(brief["bf16"]["served_qps"] / brief["f32"]["served_qps"], 3)
+    if "served_qps" in brief.get("bf16", {}) and "plain" in brief:
+        res["served_bf16_over_plain_f32_batch"] = round(brief["bf16"]["served_qps"] / brief["plain"]["batch_qps"], 3)
+    return res
 
 
 def run_serve_sweep(args):
@@ -707,8 +766,12 @@ def run_pilot(args):
         return pilot.pilot_search_ex(g, q, k, ef, o_ids, o_d, stream, options=opts, counters=counters,
                                      kernel_ms=timing)
 
-    # operating point: the smallest swept ef reaching recall@10 >= 0.95
+    # operating point: the smallest swept ef reaching recall@10 >= 0.95; one
+    # untimed call first, so the sweep's times exclude the workspace
+    # allocation and module loading of the first call
     efs = [args.ef] if args.ef else list(w.efs) + [e for e in EXTRA_EFS if e > max(w.efs)]
+    search(qd, efs[0], ids, dists, cnt)
+    torch.cuda.synchronize()
     sweep, ef = [], None
     for cand in efs:
         search(qd, cand, ids, dists, cnt)
@@ -796,6 +859,9 @@ def run_pilot(args):
         serving["capacity"] = serving_run(pilot, g, Q, gt, cap_rate, min(int(cap_rate * 0.5), 150_000),
                                           fixed_ef=ef, max_ef=512, max_k=100,
                                           expansions_per_step=args.serve_budget)
+    forms = None
+    if not args.no_forms and ws == 1:
+        forms = forms_summary(args)
     peak, peak_kind = measured_peaks()
     mean_search_ms = statistics.mean(search_ms)
     achieved = alg_bytes / (mean_search_ms / 1000.0) / 1e9
@@ -807,9 +873,7 @@ def run_pilot(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline:
-        qps, ns, secs, threads = oracle_sample(idx, Q, k, ef)
-        cpu = {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {ns} of {nq} queries, ef={ef}, {secs:.1f}s on {threads} host threads"}
+        cpu = cpu_baseline_entry(idx, Q, k, ef)
     c = counters.astype(np.float64)
     line = {
         "metric": "QPS@recall10=0.95", "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -838,6 +902,8 @@ def run_pilot(args):
         line["cpu_baseline"] = cpu
     if serving is not None:
         line["serving"] = serving
+    if forms is not None:
+        line["forms"] = forms
     print(json.dumps(line), flush=True)
     return 0
 
@@ -856,6 +922,8 @@ def main(argv=None):
     ap.add_argument("--stage-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) run")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the compact served BF16 vs FP32 comparison on the 768-d workload's prefix")
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-budget", type=int, default=1024, help="expansions per request per step")

@@ -118,9 +118,15 @@ typedef struct {
 
 /*
  * Copy an index to the current CUDA device.  *out receives the handle.  Besides
- * the arrays, the index holds the searches' visited sets: one byte per node
- * for each resident search warp (up to 16 per SM, within a quarter of the free
- * device memory), e.g. about 2.4 GB at n = 1M on a 148-SM GPU.
+ * the arrays, the index holds the searches' visited sets: one hash table per
+ * resident search warp (16 per SM) of 4 x pow2(PILOT_MAX_EF x max(R, R_sub))
+ * bytes, e.g. 64 KB per warp and 155 MB in all at degree 32 on a 148-SM GPU,
+ * whatever n is.  A search with list size ef uses pow2(max(ef, 32) x max(R,
+ * R_sub)) entries of it (at least 256).  Each set carries an epoch tag, so a
+ * new one costs nothing until the tag's epochs run out (2^(32 - bits of n-1)
+ * - 1 of them) and the table is cleared; the environment variable
+ * PILOT_VISITED_EPOCH_CYCLE=<c>, read here, shortens that cycle to c sets (a
+ * testing aid: it only clears more often).
  */
 pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
 
@@ -171,7 +177,10 @@ typedef struct {
                                    from CUDA events recorded on the call's stream */
     int32_t* status_words;      /* optional HOST array of 8 int32: [3] = queries whose FES
                                    survivors were not certified (the entry set was scanned
-                                   exactly), [0] = non-finite queries; others reserved */
+                                   exactly), [0] = non-finite queries, [7] = visited-table
+                                   insertions that found no room within 8 buckets (such a
+                                   node is scored again if met again: results unchanged, the
+                                   distance counters can exceed the oracle's); others reserved */
     int32_t fes_seeds;          /* entries seeding stage (1)'s candidate list: the best
                                    fes_seeds of the entry set by (reduced distance, id) with
                                    FES, the first fes_seeds entries without it; capped at ef
@@ -186,6 +195,12 @@ typedef struct {
                                    < n and distinct within a row (PILOT_EINVAL otherwise).
                                    Counters: [6] = seeds scored, [7] = -1 */
     int32_t seed_count;         /* entries per row of seed_ids, 1..ef */
+    int32_t visited_entries;    /* entries of the visited table this call uses per warp: 0 =
+                                   automatic (pow2(max(ef, 32) x max(R, R_sub)), at least 256),
+                                   else a cap, a power of two from 256 to the index's table
+                                   (PILOT_EINVAL otherwise).  A smaller table trades L2 reuse for
+                                   insertions that find no room (status word [7]); results do
+                                   not change */
 } pilot_search_options;
 
 void pilot_search_options_default(pilot_search_options* opt);
@@ -235,7 +250,7 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  * queued requests into free slots, then advances every request in flight by
  * at most expansions_per_step expansions of the staged search in one
  * persistent launch replayed from a CUDA graph; a request's candidate list,
- * visited bytes and phase stay in device memory between steps.  Requests
+ * visited table and phase stay in device memory between steps.  Requests
  * that arrive while others run join at a following step.  Steps are
  * pipelined two deep: the next step is enqueued before the host completes
  * the previous one.  Each request's result equals pilot_search's for the
@@ -243,8 +258,9 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  *
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
- * max_slots or what hbm_budget_bytes holds (list, query rows and one visited
- * byte per node per slot), whichever is smaller, rounded down to a multiple
+ * max_slots or what hbm_budget_bytes holds (list, query rows and a visited
+ * table of 4 x pow2(max_ef x max(R, R_sub)) bytes per slot, independent of n),
+ * whichever is smaller, rounded down to a multiple
  * of the warps the step kernel keeps resident (when it holds at least one
  * such wave), so that every step runs whole waves; further requests queue, and
  * submit returns PILOT_EBUSY when queue_capacity requests are waiting.
@@ -262,7 +278,8 @@ typedef struct {
 
 typedef struct {
     uint64_t submitted, admitted, rejected, completed, steps;
-    int32_t slots, in_flight, queued, reserved;
+    int32_t slots, in_flight, queued;
+    int32_t visited_overflows;    /* visited-table insertions that found no room (results unchanged) */
     double qps;                   /* completed / (last completion - first submission) */
     double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency */
 } pilot_serve_statistics;
@@ -278,6 +295,11 @@ pilot_status pilot_serve_submit(pilot_server* server, const float* query, int k,
  * (host memory).  PILOT_ETIMEOUT if not done in time (the ticket stays
  * valid); each finished ticket can be collected once. */
 pilot_status pilot_serve_wait(pilot_server* server, uint64_t ticket, int timeout_ms, int32_t* ids, float* dists);
+/* pilot_serve_wait that also writes the request's 8 counters (host memory,
+ * may be NULL): the same per-stage expansions and distances, re-ranked count
+ * and entry id as pilot_search_options.counters. */
+pilot_status pilot_serve_wait_ex(pilot_server* server, uint64_t ticket, int timeout_ms, int32_t* ids, float* dists,
+                                 int32_t* counters);
 pilot_status pilot_serve_stats(pilot_server* server, pilot_serve_statistics* stats);
 /* Stop the background thread and free the server (pending tickets are lost). */
 void pilot_serve_destroy(pilot_server* server);

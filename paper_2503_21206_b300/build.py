@@ -1,4 +1,7 @@
-"""Build libpilot.so (every CUDA source under csrc/) in-tree for sm_103a."""
+"""Build libpilot.so (every CUDA source under csrc/) in-tree for sm_103a.
+
+Each source compiles to its own object under _build/ (in parallel), then one
+link makes the shared library."""
 from __future__ import annotations
 
 import glob
@@ -12,6 +15,7 @@ LIB = os.path.join(HERE, "libpilot.so")
 CHECKED_LIB = os.path.join(HERE, "libpilot_checked.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
+OBJ_DIR = os.path.join(HERE, "_build")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
@@ -39,13 +43,29 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     if not force and not _stale(lib):
         return lib
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nvcc, *NVCC_FLAGS, *(["-DPILOT_CHECKED"] if checked else []), "-I", INCLUDE, "-shared", "-o", tmp,
-           *sources()]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, lib)
+    tag = f"{'checked' if checked else 'plain'}.{os.getpid()}"
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    extra = ["-DPILOT_CHECKED"] if checked else []
+    jobs, objs = [], []
+    for src in sources():
+        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + f".{tag}.o")
+        cmd = [nvcc, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        jobs.append((src, subprocess.Popen(cmd)))
+        objs.append(obj)
+    failed = [src for src, p in jobs if p.wait() != 0]
+    try:
+        if failed:
+            raise RuntimeError(f"nvcc failed on {', '.join(os.path.basename(f) for f in failed)}")
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs],
+                       check=True)
+        os.replace(tmp, lib)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return lib
 
 

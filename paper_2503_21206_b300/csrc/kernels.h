@@ -40,15 +40,48 @@ struct DevIndex {
     const float* centroids;
     const int32_t* cl_entries;
     const int32_t* cl_offsets;   // n_clusters + 1
-    // Visited sets: one byte per node for each of stamp_slots warp slots (row
-    // stride stamp_stride bytes); a node is visited in the current stage when
-    // its byte equals the slot's current epoch.  stamp_epoch holds each slot's
-    // running epoch counter across launches.
-    uint8_t* stamps;
-    uint32_t* stamp_epoch;
-    int64_t stamp_stride;
-    int stamp_slots;
+    // Visited sets: one open-addressing hash table per warp slot (vis_slots
+    // slots, vis_stride 32-bit entries each, a power of two), in buckets of 8
+    // entries (one 32-byte sector).  An entry holds (epoch << id_bits) | id;
+    // entries of another epoch are free, so a new set costs one epoch step and
+    // a slot is cleared only when its epoch counter wraps.  The size depends
+    // on ef and the degree, not on n.  vis_epoch holds each slot's running
+    // epoch counter across launches.
+    uint32_t* vis;
+    uint32_t* vis_epoch;
+    int64_t vis_stride;
+    int vis_slots;
+    int id_bits;         // bits of a node id: n - 1 < 2^id_bits
+    uint32_t epoch_max;  // epochs per cycle: at most 2^(32 - id_bits) - 1
 };
+
+constexpr int kVisBucket = 8;      // entries per bucket (32 bytes)
+constexpr int kVisMaxProbe = 8;    // buckets probed before an insertion gives up
+
+// Entries of the visited table a search with list size ef uses: the power of
+// two >= max(ef, 32) x the larger degree (at least 256).  A stage visits at
+// most (its expansions) x degree nodes, and in practice fewer than ef x
+// degree, so the table stays at most about half full.
+__host__ __device__ inline int64_t vis_entries_for(int ef, int max_degree) {
+    int64_t want = int64_t(ef < 32 ? 32 : ef) * max_degree, h = 256;
+    while (h < want) h <<= 1;
+    return h;
+}
+
+// Bucket mask and hash shift of a table of vis_entries_for(ef, max_degree)
+// entries, capped at entries_per_slot (both powers of two >= 256).
+struct VisSize {
+    uint32_t mask;
+    int shift;
+};
+__host__ __device__ inline VisSize vis_size_for(int ef, int max_degree, int64_t entries_per_slot) {
+    int64_t h = vis_entries_for(ef, max_degree);
+    if (h > entries_per_slot) h = entries_per_slot;
+    const int64_t buckets = h / kVisBucket;
+    int lg = 0;
+    while ((int64_t(1) << lg) < buckets) ++lg;
+    return VisSize{uint32_t(buckets - 1), 32 - lg};
+}
 
 struct SearchConfig {
     int k, ef;
@@ -57,6 +90,9 @@ struct SearchConfig {
     int fes_T;
     int fes_seeds;       // entries seeding stage (1) (1..kFesT)
     int stage_bytes;     // per-warp row staging buffer
+    uint32_t vis_mask;   // buckets of the visited table in use - 1 (a power of two - 1)
+    int vis_shift;       // 32 - log2(buckets): the hash keeps the top bits
+    int filter;          // 1: certified FP32 pre-filter once the list is full
 };
 
 // Per-call device buffers.
@@ -73,7 +109,9 @@ struct SearchIO {
     int32_t* counters;         // nq x 8 or null
     int32_t* bad_query;        // nq flags (non-finite input)
     int32_t* status;           // [0] non-finite queries, [1] next query, [2] gather timeouts,
-                               // [3] FES fallbacks, [4] expansion-cap hits, [5] FES kernel timeouts
+                               // [3] FES fallbacks, [4] expansion-cap hits, [5] FES kernel timeouts,
+                               // [6] out-of-range indices skipped (checked build),
+                               // [7] visited insertions that found no room
     const int32_t* seed_ids;   // nq x seed_count original ids (-1 skipped) seeding the final stage, or null
     int seed_count;
 };
@@ -107,7 +145,8 @@ struct ServeIO {
     const float* new_qp;
     const int32_t* new_fes_pos;
     const double* new_fes_lb;
-    uint8_t* stamps;             // per slot, stamp_stride bytes
+    uint32_t* vis;               // per slot, vis_stride entries of the index's layout
+    int32_t* vis_overflow;       // device counter of visited insertions that found no room
     int32_t* res_ids;            // per slot, k_max (host-mapped)
     float* res_dists;            // per slot, k_max (host-mapped)
     int32_t* res_done;           // per slot: 1 done, 2 failed (host-mapped)
@@ -143,6 +182,8 @@ size_t search_smem_per_warp(const DevIndex& ix, const SearchConfig& cfg);
 SearchConfig default_search_config(const DevIndex& ix, int k, int ef);
 // Stage `rows` rows of the widest row kind per gather pass (4..32).
 void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows);
+// Size the visited table of cfg for its ef within entries_per_slot.
+void set_visited_size(const DevIndex& ix, SearchConfig& cfg, int64_t entries_per_slot);
 
 // Internal view of a loaded index for entry points outside pilot_api.cu.
 // Search shape chosen by the autotuner for one class of ef: the candidate

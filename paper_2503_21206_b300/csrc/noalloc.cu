@@ -158,6 +158,8 @@ extern "C" pilot_status pilot_search_noalloc(pilot_index* index, const float* qu
     if (v.status_host[2]) return error(PILOT_ETIMEOUT, "%lld search warps gave up waiting for a row gather", v.status_host[2]);
     if (v.status_host[5]) return error(PILOT_ETIMEOUT, "%lld FES blocks gave up waiting for the tensor cores", v.status_host[5]);
     if (v.status_host[4]) return error(PILOT_ECUDA, "%lld queries hit the expansion cap", v.status_host[4]);
+    if (v.status_host[6])
+        return error(PILOT_ECUDA, "%lld out-of-range graph indices were skipped (checked build)", v.status_host[6]);
     if (v.status_host[0])
         return error(PILOT_EINVAL, "%lld queries hold NaN or infinity (their results are -1 / +inf)",
                      v.status_host[0]);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -148,7 +149,7 @@ extern "C" {
 
 const char* pilot_last_error(void) { return g_error.c_str(); }
 
-int pilot_abi_version(void) { return 4; }
+int pilot_abi_version(void) { return 5; }
 
 void pilot_search_options_default(pilot_search_options* opt) {
     if (!opt) return;
@@ -379,30 +380,33 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
         return s;
     }
     X.full = static_cast<const float*>(p);
-    // visited bytes: one row of n bytes per warp slot, as many slots as the
-    // search kernel can keep resident (16 warps per SM), within a quarter of
-    // the free device memory
+    // visited sets: one hash table per warp slot the search kernel can keep
+    // resident (16 per SM), each sized for the largest ef and the larger
+    // degree -- independent of n (at most 128 KB per slot)
     {
-        size_t free_b = 0, total_b = 0;
-        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        X.stamp_stride = (n + 255) / 256 * 256;
-        int64_t slots = int64_t(ix->num_sms) * 16;
-        const int64_t cap = int64_t(free_b / 4) / X.stamp_stride;
-        if (slots > cap) slots = cap;
-        if (slots < 8) return fail(PILOT_ENOMEM, "no room for the visited sets (%lld bytes per slot)",
-                                   (long long)X.stamp_stride);
-        X.stamp_slots = int(slots);
+        X.id_bits = 1;
+        while ((int64_t(1) << X.id_bits) < n) ++X.id_bits;   // n - 1 < 2^id_bits <= 2^31
+        X.epoch_max = 0xFFFFFFFFu >> X.id_bits;
+        // a shorter epoch cycle (more frequent table clears) for tests of the wrap
+        if (const char* ev = std::getenv("PILOT_VISITED_EPOCH_CYCLE")) {
+            const long long c = std::atoll(ev);
+            if (c >= 1 && uint64_t(c) < X.epoch_max) X.epoch_max = uint32_t(c);
+        }
+        X.vis_stride = vis_entries_for(PILOT_MAX_EF, std::max(X.R, X.R_sub));
+        const int64_t slots = int64_t(ix->num_sms) * 16;
+        X.vis_slots = int(slots);
+        const size_t bytes = size_t(slots) * size_t(X.vis_stride) * 4;
         void* p1 = nullptr;
-        CUDA_TRY(cudaMalloc(&p1, size_t(slots) * size_t(X.stamp_stride)));
+        CUDA_TRY(cudaMalloc(&p1, bytes));
         ix->allocs.push_back(p1);
-        CUDA_TRY(cudaMemset(p1, 0, size_t(slots) * size_t(X.stamp_stride)));
-        X.stamps = static_cast<uint8_t*>(p1);
+        CUDA_TRY(cudaMemset(p1, 0, bytes));
+        X.vis = static_cast<uint32_t*>(p1);
         void* p2 = nullptr;
         CUDA_TRY(cudaMalloc(&p2, size_t(slots) * 4));
         ix->allocs.push_back(p2);
         CUDA_TRY(cudaMemset(p2, 0, size_t(slots) * 4));
-        X.stamp_epoch = static_cast<uint32_t*>(p2);
-        ix->device_bytes += size_t(slots) * size_t(X.stamp_stride) + size_t(slots) * 4;
+        X.vis_epoch = static_cast<uint32_t*>(p2);
+        ix->device_bytes += bytes + size_t(slots) * 4;
     }
     CUDA_TRY(cudaMallocHost(&ix->status_host, 8 * sizeof(int32_t)));
     *out = guard.release();
@@ -573,6 +577,13 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     const int rows = opt.stage_rows > 0 ? opt.stage_rows : tuned.stage_rows;
     if (wpb > 0) cfg.warps_per_block = std::min(wpb, 8);
     if (rows > 0) set_stage_rows(X, cfg, rows);
+    if (opt.visited_entries != 0) {
+        const int64_t v = opt.visited_entries;
+        if (v < 256 || v > X.vis_stride || (v & (v - 1)))
+            return fail(PILOT_EINVAL, "visited_entries = %lld must be 0 or a power of two in [256, %lld]",
+                        (long long)v, (long long)X.vis_stride);
+        set_visited_size(X, cfg, v);
+    }
 
     const bool q_dev = is_device_ptr(queries);
     const bool ids_dev = is_device_ptr(out_ids), dists_dev = is_device_ptr(out_dists);

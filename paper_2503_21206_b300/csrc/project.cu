@@ -64,8 +64,13 @@ cudaError_t launch_project(const DevIndex& ix, const SearchIO& io, cudaStream_t 
         cudaError_t e = cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
     }
+    // at most 16 resident blocks per SM; the grid-stride loop covers the rest
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     int64_t blocks = (io.nq + kWarps - 1) / kWarps;
-    if (blocks > 148 * 16) blocks = 148 * 16;
+    if (blocks > int64_t(sms) * 16) blocks = int64_t(sms) * 16;
     project_kernel<<<unsigned(blocks), kWarps * 32, smem, st>>>(ix, io);
     return cudaGetLastError();
 }

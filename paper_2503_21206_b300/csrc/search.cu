@@ -1,933 +1,10 @@
-// search.cu -- the fused staged search (Sec. 4.1 stages (1)-(3), Alg. 1).
-//
-// A persistent kernel: every warp repeatedly takes the next query and runs,
-// with all per-query state in its slice of shared memory,
-//   FES check     exact distances of the FES survivors, certified against the
-//                 scoring bound, else an exact scan of the entry set (Sec. 5)
-//   stage (1)     Algorithm 1 on the subgraph with reduced rows (Sec. 4.1 (1))
-//   re-rank       full-vector distances of stage (1)'s candidates; a fresh
-//                 visited table holding exactly them (Sec. 4.1 (2))
-//   stage (2)     `stage2_expansions` expansions on the subgraph with full rows
-//   stage (3)     Algorithm 1 on the full graph with full rows, all candidates
-//                 unchecked, reusing stage (2)'s visited table (Sec. 4.1 (3))
-//   output        the first k candidates by (distance, id)
-//
-// Per-warp shared memory: the candidate list C (sorted 64-bit keys), the
-// query and projected query, and a staging buffer for gathered rows.  The
-// visited sets live in HBM: one byte per node for every warp slot, tagged with
-// a per-slot epoch so that a slot is cleared only once every 255 stages.  The
-// visited bytes of an expansion's neighbours are loaded together with their
-// rows, so the check adds no dependent memory round trip.  Distance batches: up to 32 rows,
-// each gathered into shared memory with one bulk copy completing on the warp's
-// mbarrier; eight lanes cover one 128-byte line of a row, each lane owns 8 rows
-// x its chunks, and a transposing shuffle reduction leaves each row's sum in
-// one lane.  New candidates are
-// sorted with a warp bitonic sort and merged into C by rank.
-#include <cfloat>
-
-#include "device_common.cuh"
-#include "kernels.h"
+// search.cu -- host side of the staged search: launch-shape defaults, the
+// visited-table size, and the dispatch to the kernels of each reduced-row
+// type (search_f32.cu, search_bf16.cu, search_fp8.cu; the kernels themselves
+// are in search_impl.cuh).
+#include "search_impl.cuh"
 
 namespace pilot {
-namespace {
-
-constexpr int kCand = 32;   // distance batch (rows)
-constexpr int kMaxExpansionsPerStage = 1 << 22;
-constexpr uint32_t kMaxPolls = 1u << 24;   // bound on polls of one gather's barrier
-
-struct Layout {
-    int pool_cap;      // power of two >= ef
-    int off_pool0, off_cand, off_dist, off_bar, off_sel, off_bkeys, off_q, off_qp, off_stage;
-    int per_warp;
-};
-
-__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-__host__ __device__ inline int pow2_ceil(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
-__host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchConfig& cfg) {
-    Layout L;
-    L.pool_cap = pow2_ceil(cfg.ef < 32 ? 32 : cfg.ef);
-    int o = 0;
-    L.off_pool0 = o; o += L.pool_cap * 8;
-    L.off_cand = o; o += kCand * 4;
-    L.off_dist = o; o += kCand * 4;
-    L.off_bar = o; o += 16;
-    L.off_sel = o; o += kCand * 4;
-    L.off_bkeys = o; o += kCand * 8;
-    o = round_up(o, 16);
-    L.off_q = o; o += ix.d_pad * 4;
-    L.off_qp = o; o += ix.qp_pad * 4;
-    o = round_up(o, 128);
-    L.off_stage = o; o += cfg.stage_bytes;
-    L.per_warp = round_up(o, 128);
-    return L;
-}
-
-struct Warp {
-    uint64_t* pool;
-    uint8_t* stamps;     // this warp slot's visited bytes
-    int32_t* cand;
-    int32_t* sel;        // staged rows that need an exact distance
-    float* dist;
-    uint64_t* bkeys;
-    float* q;
-    float* qp;
-    uint8_t* stage;
-    int S;          // candidates in C
-    int ef;         // this query's list size
-    int lb;         // every candidate before position lb is checked
-    uint32_t epoch_ctr;
-    uint32_t epoch;  // 1..255: the current stage's visited tag
-    int lane;
-    uint64_t* bar;      // mbarrier of this warp's row gathers
-    uint32_t phase;     // parity of the barrier phase being waited for
-    bool failed;        // a gather did not complete within kMaxPolls polls
-#ifdef PILOT_CHECKED
-    int32_t* status;    // status words: [6] counts out-of-range indices skipped (checked build)
-#endif
-};
-
-// Checked builds (-DPILOT_CHECKED) test every index read from the graph
-// before it addresses a row; an out-of-range index is counted in status
-// word 6 and skipped instead of being dereferenced.
-#ifdef PILOT_CHECKED
-#define PILOT_CHECK_INDEX(w, v, limit)                                        \
-    do {                                                                     \
-        if ((v) >= (limit)) {                                                \
-            if ((w).status) atomicAdd(&(w).status[6], 1);                    \
-            (v) = -1;                                                        \
-        }                                                                    \
-    } while (0)
-#else
-#define PILOT_CHECK_INDEX(w, v, limit) \
-    do {                               \
-    } while (0)
-#endif
-
-// Exact accumulation of one 16-byte chunk of a row into acc: the chunk holds
-// 4 FP32, 8 BF16 or 16 FP8 elements; qc points at the matching query elements;
-// sc is the row's FP8 scale.
-template <int DT, int METRIC>
-__device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, float sc) {
-    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-    if (DT == 0) {
-        const float4 qv = *reinterpret_cast<const float4*>(qc);
-        const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (METRIC == 0) l2_acc(acc, qa[e], __uint_as_float(wv[e]));
-            else ip_acc(acc, qa[e], __uint_as_float(wv[e]));
-        }
-    } else if (DT == 1) {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float2 qv = *reinterpret_cast<const float2*>(qc + h * 2);
-            const float x0 = bf16_to_f32(wv[h] & 0xFFFFu), x1 = bf16_to_f32(wv[h] >> 16);
-            if (METRIC == 0) {
-                l2_acc(acc, qv.x, x0);
-                l2_acc(acc, qv.y, x1);
-            } else {
-                ip_acc(acc, qv.x, x0);
-                ip_acc(acc, qv.y, x1);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float4 qv = *reinterpret_cast<const float4*>(qc + h * 4);
-            const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-            float c[4];
-            e4m3x4_to_f32(wv[h], c);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if (METRIC == 0) {
-                    float xl;
-                    const float xh = two_prod(c[b], sc, xl);   // code * scale = xh + xl exactly
-                    l2_acc2(acc, qa[b], xh, xl);
-                } else {
-                    ip_acc(acc, qa[b], c[b]);   // sum q * code; the row's scale is applied once at the end
-                }
-            }
-        }
-    }
-}
-
-// Transposing reduction over the eight lanes of a group: afterwards lane
-// (g, mm) holds the full sum of row slot g + 4 * mm.
-__device__ __forceinline__ DF reduce8(DF (&acc)[8], int mm) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = mm & 4;
-        const DF send = up ? acc[i] : acc[i + 4];
-        const DF keep = up ? acc[i + 4] : acc[i];
-        acc[i] = df_add(keep, df_shfl_xor(send, 4));
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = mm & 2;
-        const DF send = up ? acc[i] : acc[i + 2];
-        const DF keep = up ? acc[i + 2] : acc[i];
-        acc[i] = df_add(keep, df_shfl_xor(send, 2));
-    }
-    const bool up = mm & 1;
-    const DF send = up ? acc[0] : acc[1];
-    const DF keep = up ? acc[1] : acc[0];
-    return df_add(keep, df_shfl_xor(send, 1));
-}
-
-// Exact distances of the staged rows sel(i), i < m, into dist[sel(i)].
-// Staged row s lives at stage + s * row_bytes.  Row slots are spread as lane
-// (g, mm) -> rows g + 4 j, chunks mm + 8 t, for a warp-uniform number of slots.
-template <int DT, int METRIC, class Sel>
-__device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float* __restrict__ scales,
-                                             const float* q, int m, Sel sel, int cand_off) {
-    const int g = w.lane >> 3, mm = w.lane & 7;
-    const int F8 = row_bytes >> 7;
-    constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
-    const int jrows = (m + 3) >> 2;
-    DF acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        acc[j] = DF{0.0f, 0.0f};
-        if (j < jrows) {
-            const int i = g + 4 * j;
-            const int srow = sel(i < m ? i : 0);
-            const uint8_t* rowp = w.stage + srow * row_bytes;
-            const float sc = DT == 2 ? __ldg(scales + w.cand[cand_off + srow]) : 1.0f;
-            for (int t = 0; t < F8; ++t) {
-                const int c = mm + 8 * t;
-                exact_chunk<DT, METRIC>(acc[j], *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
-            }
-        }
-    }
-    DF sum = reduce8(acc, mm);
-    const int i = g + 4 * mm;
-    if (DT == 2 && METRIC == 1) {
-        // sum q_e (c_e s) = s * sum q_e c_e exactly; scale the pair once
-        const float s = i < m ? __ldg(scales + w.cand[cand_off + sel(i)]) : 1.0f;
-        float e;
-        const float p = two_prod(sum.hi, s, e);
-        sum = DF{p, __fmaf_rn(sum.lo, s, e)};
-    }
-    if (i < m) w.dist[cand_off + sel(i)] = df_finish(sum, METRIC);
-}
-
-// Gather rows cand[r0..r1) (r1 - r0 <= 32) into the staging buffer: lane i
-// issues one bulk copy of row r0 + i; all complete on the warp's mbarrier.
-// Rows in host memory mapped into the device's address space (`plain`) are
-// copied instead with 16-byte loads spread over all lanes.
-__device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int r0, int r1,
-                                            bool plain) {
-    const int n = r1 - r0;
-    if (plain) {
-        const int cpr = row_bytes >> 4;
-        const int total = n * cpr;
-        __syncwarp();
-#pragma unroll 4
-        for (int c = w.lane; c < total; c += 32) {
-            const int r = c / cpr, o = c - r * cpr;
-            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(w.cand[r0 + r]) * row_bytes + o * 16);
-            *reinterpret_cast<uint4*>(w.stage + r * row_bytes + o * 16) = v;
-        }
-        __syncwarp();
-        return;
-    }
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
-    __syncwarp();
-    if (w.lane < n)
-        bulk_copy_g2s(w.stage + w.lane * row_bytes, base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
-                      uint32_t(row_bytes), w.bar);
-    if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
-        // give the copies still in flight one more bounded wait, then report
-        mbar_wait(w.bar, w.phase, kMaxPolls);
-        w.failed = true;
-    }
-    w.phase ^= 1u;
-    __syncwarp();
-}
-
-// Exact distances of rows cand[0..m) of a row array (`base`, `row_bytes` per
-// row, element type DT: 0 f32, 1 bf16, 2 fp8 codes with per-row `scales`) to
-// the query q in shared memory, into dist[0..m).  Rows are gathered with one
-// bulk copy each, P at a time (as many as the staging buffer holds).
-template <int DT, int METRIC>
-__device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
-                                           const float* __restrict__ scales, const float* q, int m,
-                                           int stage_bytes, bool plain) {
-    int P = stage_bytes / row_bytes;
-    P = P >= kCand ? kCand : (P & ~3);
-    for (int r0 = 0; r0 < m; r0 += P) {
-        const int r1 = r0 + P < m ? r0 + P : m;
-        gather_rows(w, base, row_bytes, r0, r1, plain);
-        exact_staged<DT, METRIC>(w, row_bytes, scales, q, r1 - r0, [](int i) { return i; }, r0);
-        __syncwarp();
-    }
-}
-
-// Merge nb sorted new keys (lanes 0..nb-1, kKeyEmpty beyond) into C in place.
-// A new key equal to one already in C (same distance and id) is dropped.  Each
-// kept key lands at (its rank among the new keys) + (its lower bound in C);
-// output positions are filled from the last 32-slot chunk down to the first
-// changed one, every lane reading its source before any lane writes, so an
-// element is always read before it is overwritten.  C keeps its ef best.
-__device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef) {
-    const int lane = w.lane;
-    uint64_t* A = w.pool;
-    const int S = w.S;
-    // lower bound of every new key in C, in lock step (fixed step count)
-    int p = 0;
-    for (int step = S > 0 ? (1 << (31 - __clz(S))) : 0; step > 0; step >>= 1)
-        if (p + step <= S && (A[p + step - 1] & ~1ull) < key) p += step;
-    const bool dup = lane < nb && p < S && (A[p] & ~1ull) == key;
-    const bool mine = lane < nb && !dup;
-    const unsigned keep = __ballot_sync(kFull, mine);
-    const int nb2 = __popc(keep);
-    if (nb2 == 0) return;
-    const int ci = __popc(keep & lanemask_lt());
-    const int np = mine ? p + ci : 0x7FFFFFFF;
-    if (mine) w.bkeys[ci] = key;
-    const int Snew = min(S + nb2, ef);
-    const int lo_pos = __reduce_min_sync(kFull, np);
-    __syncwarp();
-    if (lo_pos >= Snew) return;
-    for (int c = (Snew - 1) >> 5; c >= (lo_pos >> 5); --c) {
-        const int base = c << 5;
-        const int pos = base + lane;
-        const unsigned bit = (mine && np >= base && np < base + 32) ? (1u << (np - base)) : 0u;
-        const unsigned mask_c = __reduce_or_sync(kFull, bit);
-        const int before = __popc(__ballot_sync(kFull, mine && np < base));
-        const bool write = pos < Snew && pos >= lo_pos;
-        uint64_t val = 0;
-        if (write) {
-            const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-            const int kle = before + __popc(mask_c & upto);
-            val = ((mask_c >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos - kle];
-        }
-        __syncwarp();
-        if (write) A[pos] = val;
-        __syncwarp();
-    }
-    w.S = Snew;
-    if (lo_pos < w.lb) w.lb = lo_pos;
-}
-
-// Ascending bitonic sort of C in place (the re-rank), padded to a power of two.
-__device__ __forceinline__ void sort_pool(Warp& w, int cap) {
-    uint64_t* A = w.pool;
-    int N = 1;
-    while (N < w.S) N <<= 1;
-    for (int i = w.S + w.lane; i < N && i < cap; i += 32) A[i] = kKeyEmpty;
-    __syncwarp();
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = w.lane; i < N; i += 32) {
-                const int l = i ^ j;
-                if (l > i) {
-                    uint64_t a = A[i], b = A[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        A[i] = b;
-                        A[l] = a;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-__device__ __forceinline__ uint64_t warp_min_key(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t x = __shfl_xor_sync(kFull, v, o);
-        v = x < v ? x : v;
-    }
-    return v;
-}
-
-enum Phase : int { kStage1 = 1, kRerank = 2, kStage2 = 3, kStage3 = 4, kDone = 5 };
-
-// Resumable per-query search state (the candidate list itself is in Warp).
-struct QState {
-    int phase, it;                      // current phase; expansions in it so far
-    int e1, d1, e2, d2, e3, d3;         // expansions / distances per stage
-    int n_rerank;
-    int fallback, capped;
-    uint64_t best;                      // FES entry key (compact id)
-};
-
-// Start a new visited set for this warp slot.  Epochs cycle through 1..255;
-// before a cycle restarts the slot's bytes are cleared.
-__device__ __forceinline__ void new_visited_set(Warp& w, int64_t stride) {
-    w.epoch_ctr += 1;
-    const uint32_t r = w.epoch_ctr % 255u;
-    if (r == 0) {
-        uint4* p = reinterpret_cast<uint4*>(w.stamps);
-        const int64_t n16 = stride >> 4;
-        for (int64_t i = w.lane; i < n16; i += 32) p[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    w.epoch = r + 1;
-    __syncwarp();
-}
-
-template <int DT, int METRIC>
-struct Searcher {
-    const DevIndex& ix;
-    const SearchConfig& cfg;
-    Warp& w;
-
-    __device__ __forceinline__ void reduced_batch(int m) {
-        batch_dist<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes, ix.red_scales, w.qp,
-                               m, cfg.stage_bytes, false);
-    }
-    __device__ __forceinline__ void full_batch(int m) {
-        batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr, w.q, m,
-                              cfg.stage_bytes, ix.full_host != 0);
-    }
-
-    // Adjacency row of node u in a view (null if it has none).
-    __device__ __forceinline__ const int32_t* adjacency(int view, int32_t u) const {
-        if (view == 1) return ix.sub_adj + int64_t(u) * ix.R_sub;
-        if (view == 2) {
-            const int32_t cu = __ldg(ix.full2sub + u);   // every stage (2) candidate is sampled
-            return cu < 0 ? nullptr : ix.sub_adj + int64_t(cu) * ix.R_sub;
-        }
-        return ix.graph + int64_t(u) * ix.R;
-    }
-
-    // One step of Algorithm 1.  view 1: subgraph + reduced rows, compact ids;
-    // view 2: subgraph + full rows, original ids; view 3: full graph + full
-    // rows.  Returns false when C has no unchecked candidate.
-    __device__ bool expand(int view, int& n_exp, int& n_dist) {
-        const int lane = w.lane;
-        int idx = -1, idx2 = -1;
-        for (int b0 = w.lb; b0 < w.S; b0 += 32) {
-            const int i = b0 + lane;
-            const bool unc = i < w.S && !(w.pool[i] & 1ull);
-            const unsigned b = __ballot_sync(kFull, unc);
-            if (b) {
-                idx = b0 + __ffs(b) - 1;
-                const unsigned b2 = b & (b - 1);
-                if (b2) idx2 = b0 + __ffs(b2) - 1;
-                break;
-            }
-        }
-        if (idx < 0) {
-            w.lb = w.S;
-            return false;
-        }
-        const uint64_t key = w.pool[idx];
-        __syncwarp();
-        if (lane == 0) w.pool[idx] = key | 1ull;
-        w.lb = idx + 1;
-        n_exp += 1;
-        const int32_t u = key_id(key);
-        const int32_t* row = adjacency(view, u);
-        const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
-        // the next expansion most likely takes the second unchecked candidate:
-        // bring its adjacency row (every 128-byte line it spans) into L2 while
-        // this one is processed
-        if (idx2 >= 0) {
-            const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
-            if (r2) {
-                const uintptr_t first = reinterpret_cast<uintptr_t>(r2) >> 7;
-                const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + (view == 3 ? ix.R : ix.R_sub)) - 1) >> 7;
-                if (uintptr_t(lane) <= last - first)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"((first + lane) << 7));
-            }
-        }
-        __syncwarp();
-        for (int b0 = 0; b0 < W; b0 += 32) {
-            const int j = b0 + lane;
-            int32_t v = j < W ? __ldg(row + j) : -1;
-            PILOT_CHECK_INDEX(w, v, view == 3 ? ix.n : ix.n_sub);
-            if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
-            PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
-            const unsigned vb = __ballot_sync(kFull, v >= 0);
-            const int m = __popc(vb);
-            if (m == 0) continue;
-            if (v >= 0) w.cand[__popc(vb & lanemask_lt())] = v;
-            __syncwarp();
-            // visited bytes of all neighbours, in flight with their rows; the
-            // distance batch covers every neighbour and the visited ones are
-            // dropped afterwards
-            const int32_t mine = lane < m ? w.cand[lane] : 0;
-            const uint32_t tag = lane < m ? uint32_t(w.stamps[mine]) : w.epoch;
-            if (view == 1)
-                reduced_batch(m);
-            else
-                full_batch(m);
-            __syncwarp();
-            const bool isnew = tag != w.epoch;
-            if (isnew) w.stamps[mine] = uint8_t(w.epoch);
-            const int cnt = __popc(__ballot_sync(kFull, isnew));
-            n_dist += cnt;
-            uint64_t k = isnew ? make_key(w.dist[lane], mine) : kKeyEmpty;
-            // a full list only admits keys below its worst one
-            if (w.S == w.ef && k >= (w.pool[w.S - 1] & ~1ull)) k = kKeyEmpty;
-            const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
-            if (nkeep == 0) continue;
-            k = warp_sort32(k, lane);
-            merge_new(w, k, nkeep, w.ef);
-        }
-        return true;
-    }
-
-    // Query rows into shared memory.
-    __device__ __forceinline__ void load_query(const float* q_pad, const float* qp) {
-        for (int i = w.lane; i < ix.d_pad; i += 32) w.q[i] = q_pad[i];
-        for (int i = w.lane; i < ix.qp_pad; i += 32) w.qp[i] = qp[i];
-        __syncwarp();
-    }
-
-    // Fast entry selection (Sec. 5) seeding stage (1) with the
-    // best `ns` entries by (reduced distance, id): exact distances of the
-    // scoring survivors, sorted; if the ns-th of them is not certified below
-    // the bound on every other entry, an exact scan of the whole entry set
-    // keeps the best ns (merged into C with ef = ns).  The clustered form
-    // (use_fes = 2) routes the query to the closest coarse cluster and scans
-    // only its entries the same way.  Without FES the seeds are the first ns
-    // entries of the set.
-    __device__ void fes(QState& st, const int32_t* fes_pos, double fes_lb) {
-        const int lane = w.lane;
-        int ns = cfg.fes_seeds < w.ef ? cfg.fes_seeds : w.ef;
-        if (int64_t(ns) > ix.n_entry) ns = int(ix.n_entry);
-        new_visited_set(w, ix.stamp_stride);
-        w.S = 0;
-        w.lb = 0;
-        bool scan = false;
-        if (cfg.use_fes == 1) {
-            const int T = cfg.fes_T;
-            const int32_t p = lane < T ? fes_pos[lane] : -1;
-            const bool valid = p >= 0 && p < ix.n_entry;
-            const unsigned vb = __ballot_sync(kFull, valid);
-            const int m = __popc(vb);
-            if (valid) w.cand[__popc(vb & lanemask_lt())] = __ldg(ix.entry + p);
-            __syncwarp();
-            reduced_batch(m);
-            __syncwarp();
-            const uint64_t key = warp_sort32(lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
-            const uint64_t kth = __shfl_sync(kFull, key, ns - 1);
-            if (m >= ns && fes_lb >= double(nextafterf(key_dist(kth), INFINITY))) {
-                if (lane < ns) w.pool[lane] = key;
-                w.S = ns;
-            } else {
-                scan = true;
-            }
-        } else if (cfg.use_fes == 0) {
-            if (lane < ns) w.cand[lane] = __ldg(ix.entry + lane);
-            __syncwarp();
-            reduced_batch(ns);
-            __syncwarp();
-            const uint64_t key = warp_sort32(lane < ns ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
-            if (lane < ns) w.pool[lane] = key;
-            w.S = ns;
-        }
-        const int32_t* scan_list = ix.entry;   // entries scanned exactly, if any
-        int64_t scan_count = ix.n_entry;
-        if (cfg.use_fes == 2) {
-            // clustered FES (Sec. 5): route to the closest centroid by
-            // (reduced distance, cluster index), then scan that cluster
-            uint64_t bestc = kKeyEmpty;
-            for (int c0 = 0; c0 < ix.n_clusters; c0 += kCand) {
-                const int mm = ix.n_clusters - c0 < kCand ? ix.n_clusters - c0 : kCand;
-                if (lane < mm) w.cand[lane] = c0 + lane;
-                __syncwarp();
-                batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.centroids), ix.cent_pad * 4, nullptr,
-                                      w.qp, mm, cfg.stage_bytes, false);
-                __syncwarp();
-                const uint64_t k = warp_min_key(lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
-                bestc = k < bestc ? k : bestc;
-                __syncwarp();
-            }
-            const int c = int(key_id(bestc));
-            const int32_t lo = __ldg(ix.cl_offsets + c), hi = __ldg(ix.cl_offsets + c + 1);
-            scan_list = ix.cl_entries + lo;
-            scan_count = hi - lo;
-            if (ns > hi - lo) ns = hi - lo;
-            scan = true;
-        }
-        if (scan) {
-            if (cfg.use_fes == 1) st.fallback = 1;
-            const int ef_keep = w.ef;
-            w.ef = ns;
-            for (int64_t e0 = 0; e0 < scan_count; e0 += kCand) {
-                const int mm = scan_count - e0 < kCand ? int(scan_count - e0) : kCand;
-                if (lane < mm) w.cand[lane] = __ldg(scan_list + e0 + lane);
-                __syncwarp();
-                reduced_batch(mm);
-                __syncwarp();
-                uint64_t k = lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
-                if (w.S == w.ef && k >= w.pool[w.S - 1]) k = kKeyEmpty;
-                const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
-                if (nkeep > 0) {
-                    k = warp_sort32(k, lane);
-                    merge_new(w, k, nkeep, ns);
-                }
-                __syncwarp();
-            }
-            w.ef = ef_keep;
-        }
-        __syncwarp();
-        st.best = w.pool[0];
-        // stage (1) starts from the seeds, all unchecked; visited = the seeds
-        if (lane < w.S) w.stamps[key_id(w.pool[lane])] = uint8_t(w.epoch);
-        w.lb = 0;
-        st.phase = kStage1;
-        st.it = 0;
-        __syncwarp();
-    }
-
-    // Re-rank (stage (2), first part): full distances of stage (1)'s
-    // candidates, a fresh visited set holding exactly their ids, C sorted.
-    __device__ void rerank() {
-        const int lane = w.lane;
-        new_visited_set(w, ix.stamp_stride);
-        for (int b0 = 0; b0 < w.S; b0 += kCand) {
-            const int m = min(kCand, w.S - b0);
-            int32_t orig = -1;
-            if (lane < m) {
-                orig = __ldg(ix.sub2full + key_id(w.pool[b0 + lane]));
-                PILOT_CHECK_INDEX(w, orig, ix.n);
-                w.cand[lane] = orig < 0 ? 0 : orig;
-            }
-            __syncwarp();
-            full_batch(m);
-            __syncwarp();
-            if (lane < m) {
-                w.pool[b0 + lane] = make_key(w.dist[lane], orig);
-                if (orig >= 0) w.stamps[orig] = uint8_t(w.epoch);
-            }
-            __syncwarp();
-        }
-        sort_pool(w, 0x7FFFFFFF);
-        w.lb = 0;
-    }
-
-    // Explicit seeds for the final stage alone (stages (1)(2) off): C starts
-    // as the given distinct original ids (-1 entries skipped) with full
-    // distances, all unchecked and visited, the best ef kept.
-    __device__ void seed_start(QState& st, const int32_t* seeds, int count) {
-        const int lane = w.lane;
-        new_visited_set(w, ix.stamp_stride);
-        w.S = 0;
-        w.lb = 0;
-        int scored = 0;
-        for (int b0 = 0; b0 < count; b0 += kCand) {
-            const int j = b0 + lane;
-            const int32_t v = j < count ? seeds[j] : -1;
-            const unsigned vb = __ballot_sync(kFull, v >= 0);
-            const int m = __popc(vb);
-            if (m == 0) continue;
-            if (v >= 0) w.cand[__popc(vb & lanemask_lt())] = v;
-            __syncwarp();
-            full_batch(m);
-            __syncwarp();
-            uint64_t k = kKeyEmpty;
-            if (lane < m) {
-                k = make_key(w.dist[lane], w.cand[lane]);
-                w.stamps[w.cand[lane]] = uint8_t(w.epoch);
-            }
-            scored += m;
-            k = warp_sort32(k, lane);
-            merge_new(w, k, m, w.ef);
-            __syncwarp();
-        }
-        st.n_rerank = scored;
-        st.best = kKeyEmpty;
-        st.phase = kStage3;
-        st.it = 0;
-        w.lb = 0;
-        __syncwarp();
-    }
-
-    // Run the staged search from its current phase for at most `budget`
-    // expansions (Sec. 4.1 stages (1)-(3); Algorithm 1 in each).
-    __device__ void advance(QState& st, int budget) {
-        while (!w.failed && st.phase != kDone) {
-            if (st.phase == kStage1) {
-                if (!cfg.stage1 || !expand(1, st.e1, st.d1)) {
-                    st.n_rerank = w.S;
-                    st.phase = kRerank;
-                } else {
-                    if (++st.it >= kMaxExpansionsPerStage) {
-                        st.capped = 1;
-                        st.n_rerank = w.S;
-                        st.phase = kRerank;
-                    }
-                    if (--budget <= 0) break;
-                }
-            } else if (st.phase == kRerank) {
-                rerank();
-                st.phase = kStage2;
-                st.it = 0;
-            } else if (st.phase == kStage2) {
-                if (st.it >= cfg.stage2_expansions || !expand(2, st.e2, st.d2)) {
-                    if (cfg.stage3) {   // stage (3): every candidate unchecked on the full graph
-                        for (int i = w.lane; i < w.S; i += 32) w.pool[i] &= ~1ull;
-                        w.lb = 0;
-                        __syncwarp();
-                        st.phase = kStage3;
-                    } else {
-                        st.phase = kDone;
-                    }
-                    st.it = 0;
-                } else {
-                    ++st.it;
-                    if (--budget <= 0) break;
-                }
-            } else {   // kStage3
-                if (!expand(3, st.e3, st.d3)) {
-                    st.phase = kDone;
-                } else {
-                    if (++st.it >= kMaxExpansionsPerStage) {
-                        st.capped = 1;
-                        st.phase = kDone;
-                    }
-                    if (--budget <= 0) break;
-                }
-            }
-        }
-    }
-
-    // The first k candidates by (distance, id), padded with -1 / +inf.
-    __device__ void write_output(const QState& st, int k, int32_t* ids, float* dists, int32_t* counters) {
-        for (int j = w.lane; j < k; j += 32) {
-            const bool ok = j < w.S && !w.failed;
-            const uint64_t kk = ok ? w.pool[j] : kKeyEmpty;
-            ids[j] = ok ? key_id(kk) : -1;
-            dists[j] = ok ? key_dist(kk) : INFINITY;
-        }
-        if (w.lane == 0 && counters) {
-            counters[0] = st.e1; counters[1] = st.d1; counters[2] = st.e2; counters[3] = st.d2;
-            counters[4] = st.e3; counters[5] = st.d3; counters[6] = st.n_rerank;
-            counters[7] = st.best == kKeyEmpty ? -1 : __ldg(ix.sub2full + key_id(st.best));
-        }
-    }
-
-    __device__ void run(int64_t q, const SearchIO& io) {
-        load_query(io.q_pad + q * ix.d_pad, io.qp + q * ix.qp_pad);
-        QState st{};
-        w.ef = cfg.ef;
-        if (io.seed_ids) seed_start(st, io.seed_ids + q * io.seed_count, io.seed_count);
-        else fes(st, io.fes_pos + q * cfg.fes_T, io.fes_lb[q]);
-        advance(st, 0x7FFFFFFF);
-        write_output(st, cfg.k, io.out_ids + q * cfg.k, io.out_dists + q * cfg.k,
-                     io.counters ? io.counters + q * 8 : nullptr);
-        if (w.lane == 0) {
-            if (st.fallback) atomicAdd(&io.status[3], 1);
-            if (st.capped) atomicAdd(&io.status[4], 1);
-        }
-        __syncwarp();
-    }
-};
-
-// Carve this warp's slice of shared memory and initialise its barrier.
-__device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem) {
-    const int warp = threadIdx.x >> 5;
-    uint8_t* base = smem + size_t(warp) * L.per_warp;
-    Warp w;
-    w.pool = reinterpret_cast<uint64_t*>(base + L.off_pool0);
-    w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
-    w.dist = reinterpret_cast<float*>(base + L.off_dist);
-    w.sel = reinterpret_cast<int32_t*>(base + L.off_sel);
-    w.bar = reinterpret_cast<uint64_t*>(base + L.off_bar);
-    w.bkeys = reinterpret_cast<uint64_t*>(base + L.off_bkeys);
-    w.q = reinterpret_cast<float*>(base + L.off_q);
-    w.qp = reinterpret_cast<float*>(base + L.off_qp);
-    w.stage = base + L.off_stage;
-    w.phase = 0;
-    w.failed = false;
-    w.lane = threadIdx.x & 31;
-    w.S = 0;
-    w.lb = 0;
-    w.ef = 0;
-    w.epoch = 0;
-    w.epoch_ctr = 0;
-    if (w.lane == 0) mbar_init(w.bar, 1);
-    __syncwarp();
-    return w;
-}
-
-template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) search_kernel(DevIndex ix, SearchConfig cfg, SearchIO io, Layout L) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    Warp w = setup_warp(L, smem);
-#ifdef PILOT_CHECKED
-    w.status = io.status;
-#endif
-    const int slot = blockIdx.x * cfg.warps_per_block + (threadIdx.x >> 5);   // < ix.stamp_slots (launch bound)
-    w.stamps = ix.stamps + int64_t(slot) * ix.stamp_stride;
-    w.epoch_ctr = ix.stamp_epoch[slot];
-    Searcher<DT, METRIC> s{ix, cfg, w};
-    for (;;) {
-        int64_t q = 0;
-        if (w.lane == 0) q = atomicAdd(&io.status[1], 1);
-        q = __shfl_sync(kFull, q, 0);
-        if (q >= io.nq) break;
-        if (io.bad_query[q]) {
-            for (int j = w.lane; j < cfg.k; j += 32) {
-                io.out_ids[q * cfg.k + j] = -1;
-                io.out_dists[q * cfg.k + j] = INFINITY;
-            }
-            continue;
-        }
-        s.run(q, io);
-        if (w.failed) {   // a gather timed out: report and stop taking queries
-            if (w.lane == 0) atomicAdd(&io.status[2], 1);
-            break;
-        }
-    }
-    if (w.lane == 0) ix.stamp_epoch[slot] = w.epoch_ctr;
-}
-
-// One serving step: every active request advances by at most sio.budget
-// expansions.  A request admitted in this step starts with FES (its
-// projection and FES scores were computed for the step's new rows); others
-// resume from their slot, and slots already finished are skipped.  Finished
-// requests write their top-k to the host-mapped result rows, mark their slot
-// done and raise their done flag.
-template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) serve_step_kernel(DevIndex ix, SearchConfig cfg, ServeIO sio, Layout L) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    Warp w = setup_warp(L, smem);
-#ifdef PILOT_CHECKED
-    w.status = nullptr;
-#endif
-    Searcher<DT, METRIC> s{ix, cfg, w};
-    const int n_active = *reinterpret_cast<const volatile int32_t*>(sio.n_active);
-    for (;;) {
-        int i = 0;
-        if (w.lane == 0) i = atomicAdd(sio.next, 1);
-        i = __shfl_sync(kFull, i, 0);
-        if (i >= n_active) break;
-        const ServeEntry e = sio.entries[i];
-        SlotState* ss = sio.state + e.slot;
-        uint64_t* gpool = sio.pool + int64_t(e.slot) * sio.pool_stride;
-        float* sq = sio.q_pad + int64_t(e.slot) * ix.d_pad;
-        float* sqp = sio.qp + int64_t(e.slot) * ix.qp_pad;
-        w.stamps = sio.stamps + int64_t(e.slot) * ix.stamp_stride;
-        w.failed = false;
-        QState st{};
-        int k;
-        if (e.new_idx >= 0) {
-            const float* nq = sio.new_q_pad + int64_t(e.new_idx) * ix.d_pad;
-            const float* nqp = sio.new_qp + int64_t(e.new_idx) * ix.qp_pad;
-            for (int j = w.lane; j < ix.d_pad; j += 32) sq[j] = nq[j];
-            for (int j = w.lane; j < ix.qp_pad; j += 32) sqp[j] = nqp[j];
-            s.load_query(nq, nqp);
-            w.epoch_ctr = ss->epoch_ctr;
-            w.ef = e.ef;
-            k = e.k;
-            s.fes(st, sio.new_fes_pos + int64_t(e.new_idx) * cfg.fes_T, sio.new_fes_lb[e.new_idx]);
-        } else {
-            // a request that finished in the previous step is listed again
-            // when the host prepared this step before seeing it finish
-            if (ss->phase == kDone) continue;
-            s.load_query(sq, sqp);
-            st.phase = ss->phase; st.it = ss->it;
-            st.e1 = ss->e1; st.d1 = ss->d1; st.e2 = ss->e2; st.d2 = ss->d2; st.e3 = ss->e3; st.d3 = ss->d3;
-            st.n_rerank = ss->n_rerank; st.fallback = ss->fallback; st.capped = ss->capped; st.best = ss->best;
-            w.S = ss->S;
-            w.lb = ss->lb;
-            w.ef = ss->ef;
-            w.epoch_ctr = ss->epoch_ctr;
-            w.epoch = ss->epoch;
-            k = ss->k;
-            for (int j = w.lane; j < w.S; j += 32) w.pool[j] = gpool[j];
-            __syncwarp();
-        }
-        s.advance(st, sio.budget);
-        if (st.phase == kDone || w.failed) {
-            s.write_output(st, k, sio.res_ids + int64_t(e.slot) * sio.k_max,
-                           sio.res_dists + int64_t(e.slot) * sio.k_max, sio.res_counters + int64_t(e.slot) * 8);
-            __syncwarp();
-            __threadfence_system();
-            if (w.lane == 0) {
-                ss->epoch_ctr = w.epoch_ctr;
-                ss->phase = kDone;
-                sio.res_done[e.slot] = w.failed ? 2 : 1;
-            }
-        } else {
-            for (int j = w.lane; j < w.S; j += 32) gpool[j] = w.pool[j];
-            if (w.lane == 0) {
-                ss->phase = st.phase; ss->it = st.it;
-                ss->e1 = st.e1; ss->d1 = st.d1; ss->e2 = st.e2; ss->d2 = st.d2; ss->e3 = st.e3; ss->d3 = st.d3;
-                ss->n_rerank = st.n_rerank; ss->fallback = st.fallback; ss->capped = st.capped; ss->best = st.best;
-                ss->S = w.S; ss->lb = w.lb; ss->ef = w.ef; ss->k = k;
-                ss->epoch_ctr = w.epoch_ctr; ss->epoch = w.epoch;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-template <int DT, int METRIC>
-cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
-                     int num_sms) {
-    const Layout L = make_layout(ix, cfg);
-    const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
-    int dev = 0, smem_max = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, METRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, METRIC>, cfg.warps_per_block * 32,
-                                                      smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t blocks = int64_t(per_sm) * num_sms;
-    if (blocks * cfg.warps_per_block > ix.stamp_slots) blocks = ix.stamp_slots / cfg.warps_per_block;
-    const int64_t need = (io.nq + cfg.warps_per_block - 1) / cfg.warps_per_block;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) return cudaSuccess;
-    search_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, io, L);
-    return cudaGetLastError();
-}
-
-template <int DT, int METRIC>
-cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
-                            size_t* smem_out) {
-    const Layout L = make_layout(ix, cfg);
-    const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
-    int dev = 0, smem_max = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(serve_step_kernel<DT, METRIC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_step_kernel<DT, METRIC>,
-                                                      cfg.warps_per_block * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t b = int64_t(per_sm) * num_sms;
-    const int64_t need = (max_warps + cfg.warps_per_block - 1) / cfg.warps_per_block;
-    *blocks = int(b > need ? need : b);
-    *smem_out = smem;
-    return cudaSuccess;
-}
-
-template <int DT, int METRIC>
-cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
-                           int blocks, size_t smem) {
-    serve_step_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, sio,
-                                                                                           make_layout(ix, cfg));
-    return cudaGetLastError();
-}
-
-}  // namespace
 
 size_t serve_smem_per_block(const DevIndex& ix, const SearchConfig& cfg) {
     return make_layout(ix, cfg).per_warp * size_t(cfg.warps_per_block);
@@ -935,26 +12,20 @@ size_t serve_smem_per_block(const DevIndex& ix, const SearchConfig& cfg) {
 
 cudaError_t prepare_serve_step(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
                                size_t* smem) {
-    switch (ix.red_dtype * 2 + ix.metric) {
-        case 0: return serve_prepare_t<0, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
-        case 1: return serve_prepare_t<0, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
-        case 2: return serve_prepare_t<1, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
-        case 3: return serve_prepare_t<1, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
-        case 4: return serve_prepare_t<2, 0>(ix, cfg, num_sms, max_warps, blocks, smem);
-        case 5: return serve_prepare_t<2, 1>(ix, cfg, num_sms, max_warps, blocks, smem);
+    switch (ix.red_dtype) {
+        case 0: return prepare_serve_step_dt0(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 1: return prepare_serve_step_dt1(ix, cfg, num_sms, max_warps, blocks, smem);
+        case 2: return prepare_serve_step_dt2(ix, cfg, num_sms, max_warps, blocks, smem);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_serve_step(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
                               int blocks, size_t smem) {
-    switch (ix.red_dtype * 2 + ix.metric) {
-        case 0: return serve_launch_t<0, 0>(ix, cfg, sio, st, blocks, smem);
-        case 1: return serve_launch_t<0, 1>(ix, cfg, sio, st, blocks, smem);
-        case 2: return serve_launch_t<1, 0>(ix, cfg, sio, st, blocks, smem);
-        case 3: return serve_launch_t<1, 1>(ix, cfg, sio, st, blocks, smem);
-        case 4: return serve_launch_t<2, 0>(ix, cfg, sio, st, blocks, smem);
-        case 5: return serve_launch_t<2, 1>(ix, cfg, sio, st, blocks, smem);
+    switch (ix.red_dtype) {
+        case 0: return launch_serve_step_dt0(ix, cfg, sio, st, blocks, smem);
+        case 1: return launch_serve_step_dt1(ix, cfg, sio, st, blocks, smem);
+        case 2: return launch_serve_step_dt2(ix, cfg, sio, st, blocks, smem);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -976,7 +47,15 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;
     stage = stage > full32 ? stage : full32;
     cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
+    cfg.filter = 1;
+    set_visited_size(ix, cfg, ix.vis_stride);
     return cfg;
+}
+
+void set_visited_size(const DevIndex& ix, SearchConfig& cfg, int64_t entries_per_slot) {
+    const VisSize v = vis_size_for(cfg.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, entries_per_slot);
+    cfg.vis_mask = v.mask;
+    cfg.vis_shift = v.shift;
 }
 
 void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {
@@ -990,14 +69,10 @@ void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
                           int num_sms) {
     if (io.nq == 0) return cudaSuccess;
-    const int key = ix.red_dtype * 2 + ix.metric;
-    switch (key) {
-        case 0: return launch_t<0, 0>(ix, cfg, io, st, num_sms);
-        case 1: return launch_t<0, 1>(ix, cfg, io, st, num_sms);
-        case 2: return launch_t<1, 0>(ix, cfg, io, st, num_sms);
-        case 3: return launch_t<1, 1>(ix, cfg, io, st, num_sms);
-        case 4: return launch_t<2, 0>(ix, cfg, io, st, num_sms);
-        case 5: return launch_t<2, 1>(ix, cfg, io, st, num_sms);
+    switch (ix.red_dtype) {
+        case 0: return launch_search_dt0(ix, cfg, io, st, num_sms);
+        case 1: return launch_search_dt1(ix, cfg, io, st, num_sms);
+        case 2: return launch_search_dt2(ix, cfg, io, st, num_sms);
         default: return cudaErrorInvalidValue;
     }
 }

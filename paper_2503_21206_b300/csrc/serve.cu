@@ -5,7 +5,7 @@
 // budget of the step kernel), projects and scores the new requests' FES
 // candidates, and replays a CUDA graph holding the step kernel: every active
 // request advances by at most `expansions_per_step` expansions of the staged
-// search, keeping its candidate list, visited bytes and phase in device
+// search, keeping its candidate list, visited table and phase in device
 // memory between steps.  Requests that arrive while others are on the GPU
 // join at a following step, so their work overlaps.  Finished requests write
 // their top-k to host-mapped memory; the thread completes their tickets and
@@ -73,6 +73,7 @@ struct Result {
     pilot_status status;
     std::vector<int32_t> ids;
     std::vector<float> dists;
+    int32_t counters[8];
 };
 
 }  // namespace
@@ -91,7 +92,9 @@ struct pilot_server {
     SlotState* state = nullptr;
     uint64_t* pool = nullptr;
     float *q_pad = nullptr, *qp = nullptr;
-    uint8_t* stamps = nullptr;
+    uint32_t* vis = nullptr;          // per slot, vis_stride entries (sized by max_ef and the degree)
+    int64_t vis_stride = 0;
+    int32_t* vis_overflow = nullptr;  // device counter
     int32_t* next = nullptr;
     float *new_q = nullptr, *new_q_pad = nullptr, *new_qp = nullptr;
     int32_t *new_pos = nullptr, *new_bad = nullptr, *new_status = nullptr;
@@ -174,7 +177,7 @@ void pilot_server::loop() {
                                  [&] { return stop || !queue.empty() || !active.empty(); });
             if (stop) return;
             if (broken != PILOT_OK) {   // fail everything still pending
-                for (Request& r : queue) results[r.ticket] = Result{broken, {}, {}};
+                for (Request& r : queue) results[r.ticket] = Result{broken, {}, {}, {}};
                 queue.clear();
                 cv_done.notify_all();
                 continue;
@@ -189,7 +192,7 @@ void pilot_server::loop() {
             in_flight[0] = in_flight[1] = false;
             std::lock_guard<std::mutex> lk(mu);
             broken = s;
-            for (int slot : active) results[slot_req[size_t(slot)].ticket] = Result{s, {}, {}};
+            for (int slot : active) results[slot_req[size_t(slot)].ticket] = Result{s, {}, {}, {}};
             active.clear();
             cv_done.notify_all();
             continue;
@@ -284,6 +287,7 @@ pilot_status pilot_server::complete(int p) {
         res.ids.assign(res_ids + size_t(slot) * size_t(cfg.max_k), res_ids + size_t(slot) * size_t(cfg.max_k) + r.k);
         res.dists.assign(res_dists + size_t(slot) * size_t(cfg.max_k),
                          res_dists + size_t(slot) * size_t(cfg.max_k) + r.k);
+        for (int i = 0; i < 8; ++i) res.counters[i] = reinterpret_cast<volatile int32_t*>(res_counters)[slot * 8 + i];
         results[r.ticket] = std::move(res);
         latencies.push_back(t - r.t_submit);
         t_last_done = t;
@@ -344,10 +348,12 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
         return err(PILOT_EINVAL, "max_ef = %lld needs more shared memory per block than the device has",
                    (long long)c.max_ef);
 
-    // HBM budget: per slot its list, query rows, state and visited bytes
+    // HBM budget: per slot its list, query rows, state and visited table
+    // (sized by max_ef and the degree, independent of n)
     const int pool_stride = [&] { int p = 32; while (p < c.max_ef) p <<= 1; return p; }();
+    S->vis_stride = vis_entries_for(int(c.max_ef), std::max(X.R, X.R_sub));
     const size_t per_slot = size_t(pool_stride) * 8 + size_t(X.d_pad + X.qp_pad) * 4 + sizeof(SlotState) +
-                            size_t(X.stamp_stride);
+                            size_t(S->vis_stride) * 4;
     size_t free_b = 0, total_b = 0;
     if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return cuda_err(e, "cudaMemGetInfo");
     const size_t budget = c.hbm_budget_bytes > 0 ? size_t(c.hbm_budget_bytes) : free_b / 4;
@@ -370,7 +376,8 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((ps = S->dalloc(&S->pool, size_t(NS) * pool_stride)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->q_pad, size_t(NS) * X.d_pad)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->qp, size_t(NS) * X.qp_pad)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->stamps, size_t(NS) * size_t(X.stamp_stride))) != PILOT_OK) return ps;
+    if ((ps = S->dalloc(&S->vis, size_t(NS) * size_t(S->vis_stride))) != PILOT_OK) return ps;
+    if ((ps = S->dalloc(&S->vis_overflow, 1)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->next, 4)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_q, size_t(NN) * X.d)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_q_pad, size_t(NN) * X.d_pad)) != PILOT_OK) return ps;
@@ -381,8 +388,9 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((ps = S->dalloc(&S->new_bad, size_t(NN))) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->new_status, 8)) != PILOT_OK) return ps;
     if ((e = cudaMemset(S->state, 0, size_t(NS) * sizeof(SlotState))) != cudaSuccess) return cuda_err(e, "clear");
-    if ((e = cudaMemset(S->stamps, 0, size_t(NS) * size_t(X.stamp_stride))) != cudaSuccess)
+    if ((e = cudaMemset(S->vis, 0, size_t(NS) * size_t(S->vis_stride) * 4)) != cudaSuccess)
         return cuda_err(e, "clear");
+    if ((e = cudaMemset(S->vis_overflow, 0, 4)) != cudaSuccess) return cuda_err(e, "clear");
     for (int p = 0; p < 2; ++p) {
         if ((ps = S->halloc(&S->entries[p], size_t(NS))) != PILOT_OK) return ps;
         if ((ps = S->halloc(&S->n_active[p], 1)) != PILOT_OK) return ps;
@@ -416,8 +424,13 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     sio.k_max = c.max_k;
     sio.budget = c.expansions_per_step;
     DevIndex XS = X;
-    XS.stamps = S->stamps;   // the server's own visited bytes, one row per slot
-    sio.stamps = S->stamps;
+    XS.vis = S->vis;   // the server's own visited tables, one per slot
+    XS.vis_stride = S->vis_stride;
+    XS.vis_slots = NS;
+    XS.vis_epoch = nullptr;   // slots keep their epoch counters in SlotState
+    set_visited_size(XS, S->scfg, S->vis_stride);
+    sio.vis = S->vis;
+    sio.vis_overflow = S->vis_overflow;
     int blocks = 0;
     size_t smem = 0;
     if ((e = prepare_serve_step(XS, S->scfg, S->view.num_sms, NS, &blocks, &smem)) != cudaSuccess)
@@ -476,6 +489,11 @@ pilot_status pilot_serve_submit(pilot_server* s, const float* q, int k, int ef, 
 }
 
 pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, int timeout_ms, int32_t* ids, float* dists) {
+    return pilot_serve_wait_ex(s, ticket, timeout_ms, ids, dists, nullptr);
+}
+
+pilot_status pilot_serve_wait_ex(pilot_server* s, uint64_t ticket, int timeout_ms, int32_t* ids, float* dists,
+                                 int32_t* counters) {
     if (!s) return err(PILOT_EINVAL, "server is NULL");
     std::unique_lock<std::mutex> lk(s->mu);
     const auto until = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
@@ -488,6 +506,7 @@ pilot_status pilot_serve_wait(pilot_server* s, uint64_t ticket, int timeout_ms, 
             if (r.status != PILOT_OK) return err(r.status, "the request failed on the GPU");
             if (ids) std::memcpy(ids, r.ids.data(), r.ids.size() * 4);
             if (dists) std::memcpy(dists, r.dists.data(), r.dists.size() * 4);
+            if (counters) std::memcpy(counters, r.counters, sizeof r.counters);
             return PILOT_OK;
         }
         if (ticket == 0 || ticket >= s->next_ticket) return err(PILOT_EINVAL, "unknown ticket %lld", (long long)ticket);
@@ -508,6 +527,9 @@ pilot_status pilot_serve_stats(pilot_server* s, pilot_serve_statistics* out) {
     out->slots = s->slots;
     out->in_flight = int32_t(s->active.size());
     out->queued = int32_t(s->queue.size());
+    int32_t ov = 0;   // read without waiting for the step in flight
+    if (cudaMemcpy(&ov, s->vis_overflow, 4, cudaMemcpyDeviceToHost) == cudaSuccess) out->visited_overflows = ov;
+    else cudaGetLastError();
     if (!s->latencies.empty()) {
         std::vector<double> l = s->latencies;
         std::sort(l.begin(), l.end());

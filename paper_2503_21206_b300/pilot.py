@@ -50,7 +50,8 @@ class pilot_search_options(ctypes.Structure):
     _fields_ = [("stage1", ctypes.c_int32), ("stage2_expansions", ctypes.c_int32), ("stage3", ctypes.c_int32),
                 ("use_fes", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("stage_rows", ctypes.c_int32),
                 ("counters", ctypes.c_void_p), ("kernel_ms", ctypes.c_void_p), ("status_words", ctypes.c_void_p),
-                ("fes_seeds", ctypes.c_int32), ("seed_ids", ctypes.c_void_p), ("seed_count", ctypes.c_int32)]
+                ("fes_seeds", ctypes.c_int32), ("seed_ids", ctypes.c_void_p), ("seed_count", ctypes.c_int32),
+                ("visited_entries", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -84,14 +85,50 @@ def _check(status: int):
 
 
 def _addr(a):
-    """Raw address of a numpy array or torch tensor (must be contiguous)."""
+    """Raw address of a numpy array or torch tensor (must be C-contiguous)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"]
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libpilot must be C-contiguous")
         return a.ctypes.data
-    assert a.is_contiguous()
+    if not a.is_contiguous():
+        raise ValueError("tensors passed to libpilot must be contiguous")
     return a.data_ptr()
+
+
+def _dtype_name(a) -> str:
+    """'float32', 'int32', ... for a numpy array or a torch tensor."""
+    return a.dtype.name if isinstance(a, np.ndarray) else str(a.dtype).split(".")[-1]
+
+
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _device_of(a):
+    """None for host memory, else the CUDA device index."""
+    if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False):
+        return None
+    return a.device.index
+
+
+def _check_search_buffers(index, queries, k: int, out_ids, out_dists, counters=None):
+    """Reject, before any pointer reaches the library, buffers whose type or
+    size would let a kernel read or write past them."""
+    d = index.dim
+    if _dtype_name(queries) != "float32" or len(queries.shape) != 2 or int(queries.shape[1]) != d:
+        raise ValueError(f"queries must be float32 of shape (nq, {d}); got {_dtype_name(queries)} "
+                         f"{tuple(queries.shape)}")
+    nq = int(queries.shape[0])
+    for name, a, dt, need in (("out_ids", out_ids, "int32", nq * k), ("out_dists", out_dists, "float32", nq * k),
+                              ("counters", counters, "int32", nq * 8)):
+        if a is None:
+            continue
+        if _dtype_name(a) != dt:
+            raise ValueError(f"{name} must be {dt}, got {_dtype_name(a)}")
+        if _numel(a) < need:
+            raise ValueError(f"{name} holds {_numel(a)} elements; nq x {need // max(nq, 1)} = {need} are written")
 
 
 def pilot_search_options_default() -> pilot_search_options:
@@ -105,6 +142,14 @@ class PilotIndex:
 
     def __init__(self, handle: int):
         self._h = ctypes.c_void_p(handle)
+        self._dim = None
+
+    @property
+    def dim(self) -> int:
+        """Dimension d of the index's vectors."""
+        if self._dim is None:
+            self._dim = int(self.info()["d"])
+        return self._dim
 
     @property
     def handle(self):
@@ -183,6 +228,7 @@ def pilot_search(index: PilotIndex, queries, k: int, ef: int, out_ids=None, out_
         out_ids = np.empty((nq, k), np.int32)
     if out_dists is None:
         out_dists = np.empty((nq, k), np.float32)
+    _check_search_buffers(index, queries, k, out_ids, out_dists, counters)
     s = None
     if stream is not None:
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -217,7 +263,11 @@ def pilot_index_free(index: PilotIndex) -> None:
 def pilot_search_noalloc(index: PilotIndex, queries, k: int, ef: int, out_ids, out_dists, stream=None):
     """pilot_search that allocates no device memory during the call: scratch
     comes from a fixed array inside the library.  ``queries``, ``out_ids`` and
-    ``out_dists`` must be CUDA tensors (device memory)."""
+    ``out_dists`` must be CUDA tensors (device memory) on one device."""
+    _check_search_buffers(index, queries, k, out_ids, out_dists)
+    devs = {_device_of(a) for a in (queries, out_ids, out_dists)}
+    if None in devs or len(devs) != 1:
+        raise ValueError("pilot_search_noalloc needs queries, out_ids and out_dists as CUDA tensors on one device")
     s = None
     if stream is not None:
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -267,7 +317,7 @@ class pilot_serve_config(ctypes.Structure):
 class pilot_serve_statistics(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("slots", ctypes.c_int32),
-                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32), ("visited_overflows", ctypes.c_int32),
                 ("qps", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double)]
 
@@ -277,6 +327,7 @@ _lib.pilot_serve_config_default.restype = None
 _lib.pilot_serve_create.argtypes = [_P, ctypes.POINTER(pilot_serve_config), ctypes.POINTER(_P)]
 _lib.pilot_serve_submit.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
 _lib.pilot_serve_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]
+_lib.pilot_serve_wait_ex.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P, _P]
 _lib.pilot_serve_stats.argtypes = [_P, ctypes.POINTER(pilot_serve_statistics)]
 _lib.pilot_serve_destroy.argtypes = [_P]
 _lib.pilot_serve_destroy.restype = None
@@ -301,16 +352,22 @@ class PilotServer:
         _check(_lib.pilot_serve_submit(self._h, q.ctypes.data, k, ef, ctypes.byref(t)))
         return t.value
 
-    def wait(self, ticket: int, k: int, timeout_ms: int = 60_000):
+    def wait(self, ticket: int, k: int, timeout_ms: int = 60_000, counters: bool = False):
+        """(ids, dists) of a ticket, plus its 8 per-stage counters with ``counters``."""
         ids = np.empty(k, np.int32)
         dists = np.empty(k, np.float32)
-        _check(_lib.pilot_serve_wait(self._h, ticket, timeout_ms, ids.ctypes.data, dists.ctypes.data))
-        return ids, dists
+        if not counters:
+            _check(_lib.pilot_serve_wait(self._h, ticket, timeout_ms, ids.ctypes.data, dists.ctypes.data))
+            return ids, dists
+        cnt = np.empty(8, np.int32)
+        _check(_lib.pilot_serve_wait_ex(self._h, ticket, timeout_ms, ids.ctypes.data, dists.ctypes.data,
+                                        cnt.ctypes.data))
+        return ids, dists, cnt
 
     def stats(self) -> dict:
         s = pilot_serve_statistics()
         _check(_lib.pilot_serve_stats(self._h, ctypes.byref(s)))
-        return {name: getattr(s, name) for name, _ in pilot_serve_statistics._fields_ if name != "reserved"}
+        return {name: getattr(s, name) for name, _ in pilot_serve_statistics._fields_}
 
     def destroy(self):
         if self._h:
@@ -339,6 +396,11 @@ def pilot_serve_submit(server: PilotServer, query, k: int, ef: int) -> int:
 
 def pilot_serve_wait(server: PilotServer, ticket: int, k: int, timeout_ms: int = 60_000):
     return server.wait(ticket, k, timeout_ms)
+
+
+def pilot_serve_wait_ex(server: PilotServer, ticket: int, k: int, timeout_ms: int = 60_000):
+    """(ids, dists, counters) of a ticket; counters as pilot_search_options.counters."""
+    return server.wait(ticket, k, timeout_ms, counters=True)
 
 
 def pilot_serve_stats(server: PilotServer) -> dict:

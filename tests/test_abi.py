@@ -42,7 +42,7 @@ def test_binding_mirrors_the_header(lib):
 def test_defaults_and_version(lib):
     o = lib.pilot_search_options_default()
     assert (o.stage1, o.stage2_expansions, o.stage3, o.use_fes) == (1, 2, 1, 1)
-    assert lib.pilot_abi_version() == 4
+    assert lib.pilot_abi_version() == 5
 
 
 def _desc_arrays(n=8, d=4, dp=2, R=2):

@@ -15,6 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CHILD = r"""
 import json, sys
 import numpy as np
+import torch
 sys.path.insert(0, ROOT)
 import oracle
 from paper_2503_21206_b300 import index_build, pilot, synth
@@ -32,8 +33,16 @@ for dtype in ("f32", "fp8"):
     oi = oracle.OracleIndex(idx.graph, idx.subgraph_mask, idx.subgraph, idx.basis, idx.reduced,
                             {"f32": 0, "bf16": 1, "fp8": 2}[dtype], idx.reduced_scales, idx.full, idx.entry_ids, 0)
     ref = oracle.search(oi, Q, 10, 64)
+    # the entry point that allocates nothing reports skipped indices the same way
+    qd = torch.from_numpy(Q).cuda()
+    ids_d = torch.empty((len(Q), 10), dtype=torch.int32, device="cuda")
+    d_d = torch.empty((len(Q), 10), dtype=torch.float32, device="cuda")
+    pilot.pilot_search_noalloc(g, qd, 10, 64, ids_d, d_d)
+    torch.cuda.synchronize()
     out[dtype] = dict(same=bool(np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
-                                and np.array_equal(cnt, ref["counters"])), skipped=int(status[6]))
+                                and np.array_equal(cnt, ref["counters"])), skipped=int(status[6]),
+                      noalloc_same=bool(np.array_equal(ids_d.cpu().numpy(), ref["ids"])
+                                        and np.array_equal(d_d.cpu().numpy(), ref["dists"])))
 print(json.dumps(out))
 """
 
@@ -51,4 +60,5 @@ def test_checked_build_matches_the_oracle():
     res = json.loads(r.stdout.strip().splitlines()[-1])
     for dtype, v in res.items():
         assert v["same"], dtype
+        assert v["noalloc_same"], dtype
         assert v["skipped"] == 0, dtype

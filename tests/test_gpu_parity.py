@@ -116,15 +116,58 @@ def test_stage_switches(c1, pilot, torch_cuda, opts):
 
 
 def test_visited_epochs_wrap(c1, pilot, torch_cuda):
-    """Visited sets are epoch-tagged bytes per warp slot, cleared once every 255
-    stages; 140 back-to-back searches (two stages each) cycle every used slot
-    through a clear.  Every repetition must return the oracle's results."""
-    w, idx, Q, _, g = c1
+    """Visited sets carry an epoch tag, and a slot's table is cleared when its
+    epochs run out.  With the cycle shortened to 3 sets
+    (PILOT_VISITED_EPOCH_CYCLE, read at load), 40 back-to-back searches (two
+    sets per query) wrap every used slot many times; every repetition must
+    return the oracle's results."""
+    w, idx, Q, _, _ = c1
+    os.environ["PILOT_VISITED_EPOCH_CYCLE"] = "3"
+    try:
+        g = pilot.load_index_data(idx)
+    finally:
+        del os.environ["PILOT_VISITED_EPOCH_CYCLE"]
     ref = oracle.search(oracle_index(idx), Q[:24], 10, 64)
-    for rep in range(140):
+    for rep in range(40):
         ids, dists, cnt = gpu_search(pilot, torch_cuda, g, Q[:24], 10, 64)
         assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"]), rep
         assert np.array_equal(cnt, ref["counters"]), rep
+    g.free()
+
+
+def test_visited_table_overflow_keeps_results(c1, pilot, torch_cuda):
+    """The exact-visited reading of Sec. 4.3: a visited insertion that finds no
+    room is treated as "not visited".  A 256-entry table cannot hold the
+    thousand-odd nodes a stage visits at ef = 128, so many insertions fail;
+    such a node is scored again when met again and the merge drops its equal
+    key, so ids, distances and expansion counts stay the oracle's, the
+    distance counts can only grow, and status word 7 counts the failures."""
+    w, idx, Q, _, g = c1
+    Qs = Q[:48]
+    ref = oracle.search(oracle_index(idx), Qs, 10, 128)
+    o = pilot.pilot_search_options_default()
+    o.visited_entries = 256
+    status = np.zeros(8, np.int32)
+    o.status_words = status.ctypes.data
+    cnt = np.empty((len(Qs), 8), np.int32)
+    ids, dists = pilot.pilot_search_ex(g, np.ascontiguousarray(Qs), 10, 128, options=o, counters=cnt)
+    assert status[7] > 0
+    assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"])
+    rc = ref["counters"]
+    for c in (0, 2, 4, 6, 7):   # expansions, re-ranked count, entry
+        assert np.array_equal(cnt[:, c], rc[:, c]), c
+    for c in (1, 3, 5):         # distances
+        assert np.all(cnt[:, c] >= rc[:, c]), c
+    assert (cnt[:, [1, 3, 5]] > rc[:, [1, 3, 5]]).any()
+    # the automatic size holds every stage: counters equal, no failure
+    o.visited_entries = 0
+    status[:] = 0
+    ids, dists = pilot.pilot_search_ex(g, np.ascontiguousarray(Qs), 10, 128, options=o, counters=cnt)
+    assert status[7] == 0 and np.array_equal(cnt, rc) and np.array_equal(ids, ref["ids"])
+    with pytest.raises(pilot.PilotError) as e:
+        o.visited_entries = 300
+        pilot.pilot_search_ex(g, np.ascontiguousarray(Qs), 10, 128, options=o)
+    assert e.value.status == pilot.PILOT_EINVAL
 
 
 def test_host_and_device_buffers_agree(c1, pilot, torch_cuda):
