@@ -119,10 +119,10 @@ typedef struct {
 /*
  * Copy an index to the current CUDA device.  *out receives the handle.  Besides
  * the arrays, the index holds the searches' visited sets: one hash table per
- * resident search warp (16 per SM) of 4 x pow2(PILOT_MAX_EF x max(R, R_sub))
- * bytes, e.g. 64 KB per warp and 155 MB in all at degree 32 on a 148-SM GPU,
- * whatever n is.  A search with list size ef uses pow2(max(ef, 32) x max(R,
- * R_sub)) entries of it (at least 256).  Each set carries an epoch tag, so a
+ * resident search warp (16 per SM) of 4 x pow2(1.25 x PILOT_MAX_EF x max(R,
+ * R_sub)) bytes, e.g. 128 KB per warp and 310 MB in all at degree 32 on a
+ * 148-SM GPU, whatever n is.  A search with list size ef uses pow2(1.25 x
+ * max(ef, 32) x max(R, R_sub)) entries of it (at least 4096).  Each set carries an epoch tag, so a
  * new one costs nothing until the tag's epochs run out (2^(32 - bits of n-1)
  * - 1 of them) and the table is cleared; the environment variable
  * PILOT_VISITED_EPOCH_CYCLE=<c>, read here, shortens that cycle to c sets (a
@@ -178,7 +178,7 @@ typedef struct {
     int32_t* status_words;      /* optional HOST array of 8 int32: [3] = queries whose FES
                                    survivors were not certified (the entry set was scanned
                                    exactly), [0] = non-finite queries, [7] = visited-table
-                                   insertions that found no room within 8 buckets (such a
+                                   insertions that found no room within 32 buckets (such a
                                    node is scored again if met again: results unchanged, the
                                    distance counters can exceed the oracle's); others reserved */
     int32_t fes_seeds;          /* entries seeding stage (1)'s candidate list: the best
@@ -196,8 +196,8 @@ typedef struct {
                                    Counters: [6] = seeds scored, [7] = -1 */
     int32_t seed_count;         /* entries per row of seed_ids, 1..ef */
     int32_t visited_entries;    /* entries of the visited table this call uses per warp: 0 =
-                                   automatic (pow2(max(ef, 32) x max(R, R_sub)), at least 256),
-                                   else a cap, a power of two from 256 to the index's table
+                                   automatic (pow2(1.25 x max(ef, 32) x max(R, R_sub)), at least
+                                   4096), else a cap, a power of two from 256 to the index's table
                                    (PILOT_EINVAL otherwise).  A smaller table trades L2 reuse for
                                    insertions that find no room (status word [7]); results do
                                    not change */
@@ -259,7 +259,7 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
  * max_slots or what hbm_budget_bytes holds (list, query rows and a visited
- * table of 4 x pow2(max_ef x max(R, R_sub)) bytes per slot, independent of n),
+ * table of 4 x pow2(1.25 x max_ef x max(R, R_sub)) bytes per slot, independent of n),
  * whichever is smaller, rounded down to a multiple
  * of the warps the step kernel keeps resident (when it holds at least one
  * such wave), so that every step runs whole waves; further requests queue, and
@@ -316,7 +316,7 @@ void pilot_serve_destroy(pilot_server* server);
  * stage3, use_fes; NULL = the defaults; its other fields are ignored), for
  * every pair of
  *   warps_per_block  in {1, 2, 4, 8}   (queries per block; one warp each)
- *   stage_rows       in {4, 8, 16, 32} (rows staged per gather pass)
+ *   stage_rows       in {8, 12, 16, 20, 24, 32} (rows staged per gather pass)
  * whose shared memory fits, and for the defaults.  The fastest becomes the
  * index's shape for that ef class: pilot_search / pilot_search_ex calls whose
  * options leave warps_per_block or stage_rows at 0, and servers created on

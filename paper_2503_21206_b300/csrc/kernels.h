@@ -56,14 +56,15 @@ struct DevIndex {
 };
 
 constexpr int kVisBucket = 8;      // entries per bucket (32 bytes)
-constexpr int kVisMaxProbe = 8;    // buckets probed before an insertion gives up
+constexpr int kVisMaxProbe = 32;   // buckets probed before an insertion gives up
 
 // Entries of the visited table a search with list size ef uses: the power of
-// two >= max(ef, 32) x the larger degree (at least 256).  A stage visits at
-// most (its expansions) x degree nodes, and in practice fewer than ef x
-// degree, so the table stays at most about half full.
+// two >= 1.25 x max(ef, 32) x the larger degree, at least 4096.  A set (stage
+// (1), or the re-rank with stages (2) and (3)) visits at most (its expansions
+// + 1) x degree nodes; measured, under 0.8 x ef x degree plus ef at ef >= 64,
+// so the table stays at most about 60% full.
 __host__ __device__ inline int64_t vis_entries_for(int ef, int max_degree) {
-    int64_t want = int64_t(ef < 32 ? 32 : ef) * max_degree, h = 256;
+    int64_t want = int64_t(ef < 32 ? 32 : ef) * max_degree * 5 / 4, h = 4096;
     while (h < want) h <<= 1;
     return h;
 }
@@ -94,6 +95,11 @@ struct SearchConfig {
     int vis_shift;       // 32 - log2(buckets): the hash keeps the top bits
     int filter;          // 1: certified FP32 pre-filter once the list is full
 };
+
+// Byte stride of gathered rows in a warp's staging buffer: 16 bytes more than
+// the row, so that lanes reading the same chunk of different rows (one row
+// per lane) fall in different shared-memory banks.
+__host__ __device__ inline int stage_stride(int row_bytes) { return row_bytes + 16; }
 
 // Per-call device buffers.
 struct SearchIO {

@@ -43,10 +43,14 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.fes_T = kFesT;
     cfg.fes_seeds = 1;
     cfg.warps_per_block = 2;
-    int stage = 4 * (ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes);
-    const int full32 = 32 * ix.full_row_bytes < 16384 ? 32 * ix.full_row_bytes : 16384;
-    stage = stage > full32 ? stage : full32;
-    cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
+    // 20 rows of the widest kind per gather pass (an expansion probes its
+    // neighbours first and gathers only the unvisited ones, typically fewer
+    // than 24 of 32), at most ~16.5 KB, at least 4 wide or 32 reduced rows
+    const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
+    int stage = 4 * (fs > rs ? fs : rs);
+    const int full20 = 20 * fs < 16896 ? 20 * fs : 16896;
+    stage = stage > full20 ? stage : full20;
+    cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
     cfg.filter = 1;
     set_visited_size(ix, cfg, ix.vis_stride);
     return cfg;
@@ -61,9 +65,9 @@ void set_visited_size(const DevIndex& ix, SearchConfig& cfg, int64_t entries_per
 void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {
     // rows of the widest row kind staged per pass (a multiple of 4, 4..32)
     rows = rows < 4 ? 4 : (rows > 32 ? 32 : rows & ~3);
-    const int widest = ix.full_row_bytes > ix.red_row_bytes ? ix.full_row_bytes : ix.red_row_bytes;
-    int stage = rows * widest;
-    cfg.stage_bytes = stage > 32 * ix.red_row_bytes ? stage : 32 * ix.red_row_bytes;
+    const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
+    int stage = rows * (fs > rs ? fs : rs);
+    cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
 }
 
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,

@@ -244,7 +244,7 @@ __device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, f
 // The kernel uses 2 (n + 8) u, twice these constants, rounds toward the safe
 // side and subtracts 1e-36 for underflow (at most n * 2^-150 in all).  The
 // bounds hold for any order of summation, so lanes may combine partial sums
-// by a butterfly.
+// in any pattern.
 // FP8 rows under L2 (code x scale rounded before the subtraction) are always
 // scored exactly.
 constexpr float kTiny = 1e-36f;
@@ -299,52 +299,38 @@ __device__ __forceinline__ void approx_chunk(float& a0, float& a1, float& b, uin
 }
 
 // Keep flags of staged rows 0..m-1: w.sel[i] = 0 when row i's certified
-// lower bound exceeds thr (it cannot enter C), else 1.  Lane (g, mm) covers
-// chunks mm + 8 t of rows g + 4 j, one row slot j at a time; cand[cand_off +
-// i] is row i's id (for the FP8 scale).
+// lower bound exceeds thr (it cannot enter C), else 1.  One row per lane:
+// lane i sums its whole row (the staging stride keeps the lanes' chunks in
+// distinct banks), so no shuffle is needed; cand[cand_off + i] is row i's id
+// (for the FP8 scale).  The caller synchronises the warp afterwards.
 template <int DT, int METRIC>
 __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float* __restrict__ scales,
                                             const float* q, int m, int cand_off, int n_elems, float thr) {
-    const int g = w.lane >> 3, mm = w.lane & 7;
-    const int F8 = row_bytes >> 7;
+    const int i = w.lane;
+    if (i >= m) return;
     constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
+    const uint8_t* rowp = w.stage + i * stage_stride(row_bytes);
+    const int nch = row_bytes >> 4;
+    float a0 = 0.0f, a1 = 0.0f, b = 0.0f;
+#pragma unroll 2
+    for (int c = 0; c < nch; ++c)
+        approx_chunk<DT, METRIC>(a0, a1, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC);
+    const float A = __fadd_rn(a0, a1);
     const float rel = float(n_elems + 8) * 1.1920928955078125e-7f;   // 2 (n + 8) u, u = 2^-24
-    const int jrows = (m + 3) >> 2;
-#pragma unroll 1
-    for (int j = 0; j < jrows; ++j) {
-        const int i = g + 4 * j;
-        const bool ok = i < m;
-        const uint8_t* rowp = w.stage + (ok ? i : 0) * row_bytes;
-        float a0 = 0.0f, a1 = 0.0f, b = 0.0f;
-#pragma unroll 1
-        for (int t = 0; t < F8; ++t) {
-            const int c = mm + 8 * t;
-            approx_chunk<DT, METRIC>(a0, a1, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC);
-        }
-        float A = __fadd_rn(a0, a1);
-        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 1));
-        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 2));
-        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 4));
-        float lb;
-        if (METRIC == 0) {
-            lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
-        } else {
-            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 1));
-            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 2));
-            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 4));
-            if (DT == 2) {
-                const float sc = __ldg(scales + w.cand[cand_off + (ok ? i : 0)]);
-                lb = __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
-            } else {
-                lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
-            }
-        }
-        if (ok && mm == 0) w.sel[i] = lb > thr ? 0 : 1;
+    float lb;
+    if (METRIC == 0) {
+        lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
+    } else if (DT == 2) {
+        const float sc = __ldg(scales + w.cand[cand_off + i]);
+        lb = __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
+    } else {
+        lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
     }
+    w.sel[i] = lb > thr ? 0 : 1;
 }
 
 // Exact distances of the staged rows sel(i), i < m, into dist[sel(i)].
-// Staged row s lives at stage + s * row_bytes.  Lane (g, mm) covers chunks
+// Staged row s lives at stage + s * stage_stride(row_bytes).  Lane (g, mm) covers chunks
 // mm + 8 t of rows g + 4 j; one row slot j at a time (a warp-uniform loop,
 // kept compact so that the search's inner loop stays in the instruction
 // cache), the eight lanes of a row combining their pairs by a butterfly.
@@ -361,7 +347,7 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
         const int i = g + 4 * j;
         const bool ok = i < m;
         const int srow = sel(ok ? i : 0);
-        const uint8_t* rowp = w.stage + srow * row_bytes;
+        const uint8_t* rowp = w.stage + srow * stage_stride(row_bytes);
         const float sc = DT == 2 ? __ldg(scales + w.cand[cand_off + srow]) : 1.0f;
         DF acc{0.0f, 0.0f};
 #pragma unroll 1
@@ -395,7 +381,7 @@ __device__ __noinline__ void gather_rows_plain(uint8_t* stage, const uint8_t* __
     for (int c = lane; c < total; c += 32) {
         const int r = c / cpr, o = c - r * cpr;
         const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(cand[r]) * row_bytes + o * 16);
-        *reinterpret_cast<uint4*>(stage + r * row_bytes + o * 16) = v;
+        *reinterpret_cast<uint4*>(stage + r * stage_stride(row_bytes) + o * 16) = v;
     }
     __syncwarp();
 }
@@ -412,7 +398,7 @@ __device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__
     if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
     __syncwarp();
     if (w.lane < n)
-        bulk_copy_g2s(w.stage + w.lane * row_bytes, base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
+        bulk_copy_g2s(w.stage + w.lane * stage_stride(row_bytes), base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
                       uint32_t(row_bytes), w.bar);
     if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
         // give the copies still in flight one more bounded wait, then report
@@ -431,7 +417,7 @@ template <int DT, int METRIC>
 __device__ __forceinline__ void batch_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
                                            const float* __restrict__ scales, const float* q, int m,
                                            int stage_bytes, bool plain) {
-    int P = stage_bytes / row_bytes;
+    int P = stage_bytes / stage_stride(row_bytes);
     P = P >= kCand ? kCand : (P & ~3);
     for (int r0 = 0; r0 < m; r0 += P) {
         const int r1 = r0 + P < m ? r0 + P : m;
@@ -448,7 +434,7 @@ template <int DT, int METRIC>
 __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
                                               const float* __restrict__ scales, const float* q, int m,
                                               int stage_bytes, bool plain, bool filter, float thr, int n_elems) {
-    int P = stage_bytes / row_bytes;
+    int P = stage_bytes / stage_stride(row_bytes);
     P = P >= kCand ? kCand : (P & ~3);
     for (int r0 = 0; r0 < m; r0 += P) {
         const int r1 = r0 + P < m ? r0 + P : m;
@@ -470,6 +456,24 @@ __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict
         if (m2 > 0) exact_staged<DT, METRIC>(w, row_bytes, scales, q, m2, [&](int i) { return w.sel[i]; }, r0);
         __syncwarp();
     }
+}
+
+// The nkeep (<= 8) keys held by some lanes (kKeyEmpty elsewhere), sorted
+// into lanes 0..nkeep-1: each key's rank is counted against the others (the
+// keys are distinct), cheaper than the 32-lane sorting network for a few keys.
+__device__ __forceinline__ uint64_t place_few(Warp& w, uint64_t key, int nkeep) {
+    const bool has = key != kKeyEmpty;
+    const unsigned hm = __ballot_sync(kFull, has);
+    if (has) w.bkeys[__popc(hm & lanemask_lt())] = key;
+    __syncwarp();
+    int rank = 0;
+    for (int j = 0; j < nkeep; ++j) rank += w.bkeys[j] < key;
+    __syncwarp();
+    if (has) w.bkeys[rank] = key;
+    __syncwarp();
+    const uint64_t out = w.lane < nkeep ? w.bkeys[w.lane] : kKeyEmpty;
+    __syncwarp();
+    return out;
 }
 
 // Merge nb sorted new keys (lanes 0..nb-1, kKeyEmpty beyond) into C in place.
@@ -642,8 +646,8 @@ struct Searcher {
         const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
         // the next expansion most likely takes the second unchecked candidate:
         // read its adjacency row now (the load completes while this expansion
-        // runs) and, once this one is done, bring its neighbours' visited-table
-        // buckets into L2, so that the next probe mostly hits L2
+        // probes), then bring its neighbours' visited-table buckets into L2, so
+        // that the next probe mostly hits L2
         int32_t ahead = -1;
         if (idx2 >= 0) {
             const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
@@ -660,6 +664,11 @@ struct Searcher {
             // the visited probe comes first: only unvisited neighbours are
             // gathered and scored
             const bool isnew = visit(w, v, v >= 0);
+            // the look-ahead row has arrived by now: prefetch its buckets so that
+            // they travel while this expansion scores its rows (stage (2)'s rows
+            // hold compact ids; it runs only 2 expansions)
+            if (b0 == 0 && view != 2 && ahead >= 0)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(w.vis + size_t(vis_bucket(w, ahead)) * kVisBucket));
             const unsigned nb = __ballot_sync(kFull, isnew);
             const int m = __popc(nb);
             n_dist += m;
@@ -687,11 +696,9 @@ struct Searcher {
             if (k >= worst) k = kKeyEmpty;
             const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
             if (nkeep == 0) continue;
-            k = warp_sort32(k, lane);
+            k = nkeep <= 8 ? place_few(w, k, nkeep) : warp_sort32(k, lane);
             merge_new(w, k, nkeep, w.ef);
         }
-        if (view != 2 && ahead >= 0)   // stage (2)'s rows hold compact ids; it runs only 2 expansions
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(w.vis + size_t(vis_bucket(w, ahead)) * kVisBucket));
         return true;
     }
 
