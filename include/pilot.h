@@ -246,34 +246,37 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
 
 /*
  * Serving (continuous batching).  A server owns device state for `slots`
- * requests in flight and runs steps on a background thread: each step admits
- * queued requests into free slots, then advances every request in flight by
- * at most expansions_per_step expansions of the staged search in one
- * persistent launch replayed from a CUDA graph; a request's candidate list,
- * visited table and phase stay in device memory between steps.  Requests
- * that arrive while others run join at a following step.  Steps are
- * pipelined two deep: the next step is enqueued before the host completes
- * the previous one.  Each request's result equals pilot_search's for the
- * same query, k and ef.
+ * requests in flight and drives `streams` lanes from a background thread.
+ * Each lane is a CUDA stream with its own sequence of steps: a step admits
+ * queued requests into free slots, then advances the lane's requests by at
+ * most expansions_per_step expansions of the staged search in one persistent
+ * launch replayed from a CUDA graph; a request's candidate list, visited
+ * table and phase stay in device memory between steps.  A request stays on
+ * its lane until it finishes, so lanes whose steps run at the same time hold
+ * disjoint slots.  Requests that arrive while steps run are admitted by the
+ * next idle lane and run beside them.  Each request's result equals
+ * pilot_search's for the same query, k and ef.
  *
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
  * max_slots or what hbm_budget_bytes holds (list, query rows and a visited
  * table of 4 x pow2(1.25 x max_ef x max(R, R_sub)) bytes per slot, independent of n),
- * whichever is smaller, rounded down to a multiple
- * of the warps the step kernel keeps resident (when it holds at least one
- * such wave), so that every step runs whole waves; further requests queue, and
- * submit returns PILOT_EBUSY when queue_capacity requests are waiting.
+ * whichever is smaller, rounded down to a multiple of the warps the step
+ * kernel keeps resident (when it holds at least one such wave); further
+ * requests queue, and submit returns PILOT_EBUSY when queue_capacity
+ * requests are waiting.  PILOT_EINVAL for streams outside 1..16.
  */
 typedef struct {
-    int32_t max_slots;            /* requests in flight at most (default 4096) */
+    int32_t max_slots;            /* requests in flight at most (default 16384) */
     int32_t max_ef;               /* largest ef a request may use (default 512) */
     int32_t max_k;                /* largest k (default 100) */
-    int32_t expansions_per_step;  /* per request per step (default 512) */
+    int32_t expansions_per_step;  /* per request per step (default 4096) */
     int32_t max_new_per_step;     /* admissions per step (default 8192; at most the slot count) */
     int32_t step_timeout_ms;      /* a step longer than this fails the server (default 10000) */
     int64_t queue_capacity;       /* waiting requests before PILOT_EBUSY (default 2^20) */
     int64_t hbm_budget_bytes;     /* device memory for slots; 0 = a quarter of free memory */
+    int32_t streams;              /* lanes: CUDA streams with their own step sequences (1..16,
+                                     default 4; 0 reads as 4) */
 } pilot_serve_config;
 
 typedef struct {
@@ -291,6 +294,13 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
  * PILOT_EINVAL for k / ef outside the admission limits or a non-finite
  * value; PILOT_EBUSY when the queue is full. */
 pilot_status pilot_serve_submit(pilot_server* server, const float* query, int k, int ef, uint64_t* ticket);
+/* Queue n queries at once (n x d floats, host memory, copied) with their own
+ * k[i] and ef[i] (host arrays); tickets[i] receives each ticket.  All or
+ * nothing: PILOT_EINVAL if any request is outside the admission limits or
+ * holds a non-finite value, PILOT_EBUSY if the queue cannot take all n; then
+ * nothing is queued. */
+pilot_status pilot_serve_submit_batch(pilot_server* server, const float* queries, int64_t n, const int32_t* k,
+                                      const int32_t* ef, uint64_t* tickets);
 /* Wait up to timeout_ms for a ticket; on success write k ids and distances
  * (host memory).  PILOT_ETIMEOUT if not done in time (the ticket stays
  * valid); each finished ticket can be collected once. */

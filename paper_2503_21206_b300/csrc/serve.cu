@@ -1,21 +1,21 @@
 // serve.cu -- continuous-batching search server (pilot_serve_* in pilot.h).
 //
-// A background thread runs steps.  Each step admits queued requests into free
-// slots (slot count set by the HBM budget, ef bounded by the shared-memory
-// budget of the step kernel), projects and scores the new requests' FES
-// candidates, and replays a CUDA graph holding the step kernel: every active
-// request advances by at most `expansions_per_step` expansions of the staged
-// search, keeping its candidate list, visited table and phase in device
-// memory between steps.  Requests that arrive while others are on the GPU
-// join at a following step, so their work overlaps.  Finished requests write
-// their top-k to host-mapped memory; the thread completes their tickets and
-// records submit-to-completion latency.
+// A background thread drives K CUDA streams ("lanes"), each with its own
+// sequence of steps.  A step admits queued requests into free slots (slot
+// count set by the HBM budget, ef bounded by the shared-memory budget of the
+// step kernel), projects and scores the new requests' FES candidates, and
+// replays a CUDA graph holding the step kernel: every request of the step
+// advances by at most `expansions_per_step` expansions of the staged search,
+// keeping its candidate list, visited table and phase in device memory.
+// Finished requests write their top-k to host-mapped memory; the thread
+// completes their tickets and records submit-to-completion latency.
 //
-// Steps are pipelined two deep: the thread prepares and enqueues step N+1
-// (its own host-mapped entry list, staging rows and captured graph) before it
-// waits for step N and completes N's requests, so the GPU does not idle
-// while the host works.  Step N+1 may list requests that finish in step N;
-// the step kernel skips slots whose state is already done.
+// A request stays on the lane that admitted it until it finishes: one that
+// outlives its step is listed again in the lane's next step, so steps that
+// run at the same time on different lanes hold disjoint slots.  Requests that
+// arrive while steps run are admitted by the next idle lane, so their work
+// overlaps on the device with the steps in flight and no step waits for
+// another's tail.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,7 +86,27 @@ struct pilot_server {
     SearchConfig scfg{};
     int slots = 0;
 
-    // device state
+    // One stream with its own step sequence: its step graph, host-mapped
+    // entry list, and buffers for the requests it admits.
+    struct Lane {
+        cudaStream_t stream = nullptr;
+        cudaGraphExec_t graph = nullptr;
+        cudaEvent_t done = nullptr;
+        bool in_flight = false;
+        double t_launch = 0.0;
+        ServeEntry* entries = nullptr;    // host-mapped, one per slot at most
+        int32_t* n_active = nullptr;      // host-mapped
+        int32_t* next = nullptr;          // device counter, zeroed by the graph
+        float* staging_q = nullptr;       // pinned, new requests' vectors
+        float *new_q = nullptr, *new_q_pad = nullptr, *new_qp = nullptr;
+        int32_t *new_pos = nullptr, *new_bad = nullptr, *new_status = nullptr;
+        uint16_t* new_qpb = nullptr;
+        double* new_lb = nullptr;
+        std::vector<int> owned;           // slots whose requests run on this lane
+    };
+    std::vector<Lane> lanes;
+
+    // device state, one entry per slot
     std::vector<void*> dev_allocs;
     std::vector<void*> host_allocs;
     SlotState* state = nullptr;
@@ -95,22 +115,8 @@ struct pilot_server {
     uint32_t* vis = nullptr;          // per slot, vis_stride entries (sized by max_ef and the degree)
     int64_t vis_stride = 0;
     int32_t* vis_overflow = nullptr;  // device counter
-    int32_t* next = nullptr;
-    float *new_q = nullptr, *new_q_pad = nullptr, *new_qp = nullptr;
-    int32_t *new_pos = nullptr, *new_bad = nullptr, *new_status = nullptr;
-    uint16_t* new_qpb = nullptr;
-    double* new_lb = nullptr;
-    // host-mapped; entry lists, counts and staging rows per step parity
-    ServeEntry* entries[2] = {nullptr, nullptr};
-    int32_t* n_active[2] = {nullptr, nullptr};
-    int32_t *res_ids = nullptr, *res_done = nullptr, *res_counters = nullptr;
+    int32_t *res_ids = nullptr, *res_done = nullptr, *res_counters = nullptr;   // host-mapped
     float* res_dists = nullptr;
-    float* staging_q[2] = {nullptr, nullptr};   // pinned, new requests' vectors
-
-    cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    cudaEvent_t step_done[2] = {nullptr, nullptr};
-    bool in_flight[2] = {false, false};
 
     // host state
     std::thread worker;
@@ -120,7 +126,6 @@ struct pilot_server {
     std::unordered_map<uint64_t, Result> results;
     std::vector<Request> slot_req;      // request occupying each slot
     std::vector<int> free_slots;
-    std::vector<int> active;            // occupied slots
     uint64_t next_ticket = 1;
     bool stop = false;
     pilot_status broken = PILOT_OK;
@@ -150,31 +155,53 @@ struct pilot_server {
     }
 
     ~pilot_server() {
-        if (stream) cudaStreamSynchronize(stream);
-        for (int p = 0; p < 2; ++p) {
-            if (graph[p]) cudaGraphExecDestroy(graph[p]);
-            if (step_done[p]) cudaEventDestroy(step_done[p]);
+        for (Lane& L : lanes)
+            if (L.stream) cudaStreamSynchronize(L.stream);
+        for (Lane& L : lanes) {
+            if (L.graph) cudaGraphExecDestroy(L.graph);
+            if (L.done) cudaEventDestroy(L.done);
+            if (L.stream) cudaStreamDestroy(L.stream);
         }
-        if (stream) cudaStreamDestroy(stream);
         for (void* p : dev_allocs) cudaFree(p);
         for (void* p : host_allocs) cudaFreeHost(p);
     }
 
+    size_t in_flight_requests() const {
+        size_t n = 0;
+        for (const Lane& L : lanes) n += L.owned.size();
+        return n;
+    }
     void loop();
-    pilot_status enqueue(int p, bool* launched);
-    pilot_status complete(int p);
+    pilot_status enqueue(int k, bool* launched);
+    pilot_status complete(int k);
+    void fail_all(pilot_status s);
 };
+
+// Fail every request still owned by a lane or waiting (after an error).
+void pilot_server::fail_all(pilot_status s) {
+    for (Lane& L : lanes)
+        if (L.stream) cudaStreamSynchronize(L.stream);
+    std::lock_guard<std::mutex> lk(mu);
+    broken = s;
+    for (Lane& L : lanes) {
+        L.in_flight = false;
+        for (int slot : L.owned) results[slot_req[size_t(slot)].ticket] = Result{s, {}, {}, {}};
+        L.owned.clear();
+    }
+    for (Request& r : queue) results[r.ticket] = Result{s, {}, {}, {}};
+    queue.clear();
+    cv_done.notify_all();
+}
 
 void pilot_server::loop() {
     cudaSetDevice(view.device);
-    int p = 0;   // parity of the next step to enqueue
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(mu);
-            const bool busy = in_flight[0] || in_flight[1];
-            if (!busy)
-                cv_work.wait_for(lk, std::chrono::milliseconds(50),
-                                 [&] { return stop || !queue.empty() || !active.empty(); });
+            bool busy = false;
+            for (const Lane& L : lanes) busy = busy || L.in_flight;
+            if (!busy && queue.empty() && in_flight_requests() == 0)
+                cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return stop || !queue.empty(); });
             if (stop) return;
             if (broken != PILOT_OK) {   // fail everything still pending
                 for (Request& r : queue) results[r.ticket] = Result{broken, {}, {}, {}};
@@ -182,42 +209,56 @@ void pilot_server::loop() {
                 cv_done.notify_all();
                 continue;
             }
-            if (!busy && queue.empty() && active.empty()) continue;
         }
-        bool launched = false;
-        pilot_status s = enqueue(p, &launched);
-        if (s == PILOT_OK && in_flight[p ^ 1]) s = complete(p ^ 1);
+        bool progress = false;
+        pilot_status s = PILOT_OK;
+        // finished steps first: they free slots for the launches below
+        for (int k = 0; k < int(lanes.size()) && s == PILOT_OK; ++k) {
+            Lane& L = lanes[size_t(k)];
+            if (!L.in_flight) continue;
+            const cudaError_t e = cudaEventQuery(L.done);
+            if (e == cudaSuccess) {
+                s = complete(k);
+                progress = true;
+            } else if (e != cudaErrorNotReady) {
+                s = cuda_err(e, "serving step");
+            } else if (now_ms() - L.t_launch > double(cfg.step_timeout_ms)) {
+                s = err(PILOT_ETIMEOUT, "a serving step ran longer than %lld ms", (long long)cfg.step_timeout_ms);
+            }
+        }
+        for (int k = 0; k < int(lanes.size()) && s == PILOT_OK; ++k) {
+            if (lanes[size_t(k)].in_flight) continue;
+            bool launched = false;
+            s = enqueue(k, &launched);
+            progress = progress || launched;
+        }
         if (s != PILOT_OK) {
-            if (stream) cudaStreamSynchronize(stream);
-            in_flight[0] = in_flight[1] = false;
-            std::lock_guard<std::mutex> lk(mu);
-            broken = s;
-            for (int slot : active) results[slot_req[size_t(slot)].ticket] = Result{s, {}, {}, {}};
-            active.clear();
-            cv_done.notify_all();
+            fail_all(s);
             continue;
         }
-        if (launched) p ^= 1;
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
-// Prepare and enqueue a step on parity p: admit queued requests into free
-// slots, list every occupied slot, upload, project and score the new ones,
-// and launch the step graph.  Nothing is launched when no slot is occupied.
-pilot_status pilot_server::enqueue(int p, bool* launched) {
+// Prepare and launch a step on lane k: the lane's unfinished requests plus
+// queued requests admitted into free slots; upload, project and score the new
+// ones, and replay the lane's step graph.  Nothing is launched when the lane
+// has nothing to run.
+pilot_status pilot_server::enqueue(int k, bool* launched) {
     *launched = false;
+    Lane& L = lanes[size_t(k)];
     int n_new = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
         int n = 0;
         const int cap_new = std::min<int>(int(free_slots.size()), cfg.max_new_per_step);
-        ServeEntry* E = entries[p];
+        ServeEntry* E = L.entries;
         while (!queue.empty() && n_new < cap_new) {
             Request r = std::move(queue.front());
             queue.pop_front();
             const int slot = free_slots.back();
             free_slots.pop_back();
-            std::memcpy(staging_q[p] + size_t(n_new) * size_t(X.d), r.q.data(), size_t(X.d) * 4);
+            std::memcpy(L.staging_q + size_t(n_new) * size_t(X.d), r.q.data(), size_t(X.d) * 4);
             reinterpret_cast<volatile int32_t*>(res_done)[slot] = 0;
             E[n++] = ServeEntry{slot, n_new, r.k, r.ef};
             r.q.clear();
@@ -225,57 +266,50 @@ pilot_status pilot_server::enqueue(int p, bool* launched) {
             ++n_new;
             ++admitted;
         }
-        for (int slot : active) E[n++] = ServeEntry{slot, -1, slot_req[size_t(slot)].k, slot_req[size_t(slot)].ef};
-        for (int i = 0; i < n_new; ++i) active.push_back(E[i].slot);
-        *reinterpret_cast<volatile int32_t*>(n_active[p]) = n;
+        for (int slot : L.owned) E[n++] = ServeEntry{slot, -1, slot_req[size_t(slot)].k, slot_req[size_t(slot)].ef};
+        for (int i = 0; i < n_new; ++i) L.owned.push_back(E[i].slot);
+        *reinterpret_cast<volatile int32_t*>(L.n_active) = n;
         if (n == 0) return PILOT_OK;
     }
     cudaError_t e;
     if (n_new > 0) {
-        if ((e = cudaMemcpyAsync(new_q, staging_q[p], size_t(n_new) * size_t(X.d) * 4, cudaMemcpyHostToDevice,
-                                 stream)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(L.new_q, L.staging_q, size_t(n_new) * size_t(X.d) * 4, cudaMemcpyHostToDevice,
+                                 L.stream)) != cudaSuccess)
             return cuda_err(e, "copy new requests");
-        if ((e = cudaMemsetAsync(new_status, 0, 8 * 4, stream)) != cudaSuccess) return cuda_err(e, "clear status");
+        if ((e = cudaMemsetAsync(L.new_status, 0, 8 * 4, L.stream)) != cudaSuccess) return cuda_err(e, "clear status");
         SearchIO io{};
         io.nq = n_new;
-        io.queries = new_q;
-        io.q_pad = new_q_pad;
-        io.qp = new_qp;
-        io.fes_pos = new_pos;
-        io.qp_bf16 = new_qpb;
-        io.fes_lb = new_lb;
-        io.bad_query = new_bad;
-        io.status = new_status;
-        if ((e = launch_project(X, io, stream)) != cudaSuccess) return cuda_err(e, "projection kernel");
-        if (scfg.use_fes && (e = launch_fes_mma(X, io, stream)) != cudaSuccess)
+        io.queries = L.new_q;
+        io.q_pad = L.new_q_pad;
+        io.qp = L.new_qp;
+        io.fes_pos = L.new_pos;
+        io.qp_bf16 = L.new_qpb;
+        io.fes_lb = L.new_lb;
+        io.bad_query = L.new_bad;
+        io.status = L.new_status;
+        if ((e = launch_project(X, io, L.stream)) != cudaSuccess) return cuda_err(e, "projection kernel");
+        if (scfg.use_fes && (e = launch_fes_mma(X, io, L.stream)) != cudaSuccess)
             return cuda_err(e, "FES tensor-core kernel");
     }
-    if ((e = cudaGraphLaunch(graph[p], stream)) != cudaSuccess) return cuda_err(e, "step graph");
-    if ((e = cudaEventRecord(step_done[p], stream)) != cudaSuccess) return cuda_err(e, "record step");
-    in_flight[p] = true;
+    if ((e = cudaGraphLaunch(L.graph, L.stream)) != cudaSuccess) return cuda_err(e, "step graph");
+    if ((e = cudaEventRecord(L.done, L.stream)) != cudaSuccess) return cuda_err(e, "record step");
+    L.in_flight = true;
+    L.t_launch = now_ms();
     *launched = true;
     return PILOT_OK;
 }
 
-// Wait (bounded) for the step on parity p, then complete every occupied slot
-// whose done flag is raised.
-pilot_status pilot_server::complete(int p) {
-    const double deadline = now_ms() + double(cfg.step_timeout_ms);
-    for (;;) {
-        cudaError_t e = cudaEventQuery(step_done[p]);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorNotReady) return cuda_err(e, "serving step");
-        if (now_ms() > deadline) return err(PILOT_ETIMEOUT, "a serving step ran longer than %lld ms",
-                                            (long long)cfg.step_timeout_ms);
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-    in_flight[p] = false;
+// Complete every request of lane k's finished step whose done flag is raised;
+// the others stay with the lane for its next step.
+pilot_status pilot_server::complete(int k) {
+    Lane& L = lanes[size_t(k)];
+    L.in_flight = false;
     const double t = now_ms();
     std::lock_guard<std::mutex> lk(mu);
     ++steps;
     std::vector<int> still;
-    still.reserve(active.size());
-    for (int slot : active) {
+    still.reserve(L.owned.size());
+    for (int slot : L.owned) {
         const int done = reinterpret_cast<volatile int32_t*>(res_done)[slot];
         if (!done) {
             still.push_back(slot);
@@ -294,7 +328,7 @@ pilot_status pilot_server::complete(int p) {
         ++completed;
         free_slots.push_back(slot);
     }
-    active.swap(still);
+    L.owned.swap(still);
     cv_done.notify_all();
     return PILOT_OK;
 }
@@ -304,13 +338,14 @@ extern "C" {
 void pilot_serve_config_default(pilot_serve_config* c) {
     if (!c) return;
     std::memset(c, 0, sizeof *c);
-    c->max_slots = 4096;
+    c->max_slots = 16384;
     c->max_ef = 512;
     c->max_k = 100;
-    c->expansions_per_step = 512;
+    c->expansions_per_step = 4096;
     c->max_new_per_step = 8192;
     c->queue_capacity = 1 << 20;
     c->step_timeout_ms = 10000;
+    c->streams = 4;
 }
 
 pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* config, pilot_server** out) {
@@ -324,6 +359,8 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if (c.expansions_per_step < 1) return err(PILOT_EINVAL, "expansions_per_step must be >= 1");
     if (c.max_new_per_step < 1 || c.queue_capacity < 1 || c.step_timeout_ms < 1 || c.max_slots < 1)
         return err(PILOT_EINVAL, "max_slots, max_new_per_step, queue_capacity and step_timeout_ms must be >= 1");
+    if (c.streams == 0) c.streams = 4;
+    if (c.streams < 1 || c.streams > 16) return err(PILOT_EINVAL, "streams = %lld must be in [1, 16]", c.streams);
     auto* S = new pilot_server();
     std::unique_ptr<pilot_server> guard(S);
     S->index = index;
@@ -378,45 +415,23 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((ps = S->dalloc(&S->qp, size_t(NS) * X.qp_pad)) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->vis, size_t(NS) * size_t(S->vis_stride))) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->vis_overflow, 1)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->next, 4)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_q, size_t(NN) * X.d)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_q_pad, size_t(NN) * X.d_pad)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_qp, size_t(NN) * X.qp_pad)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_pos, size_t(NN) * S->scfg.fes_T)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_qpb, size_t((NN + 127) / 128 * 128) * X.qp_pad)) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_lb, size_t(NN))) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_bad, size_t(NN))) != PILOT_OK) return ps;
-    if ((ps = S->dalloc(&S->new_status, 8)) != PILOT_OK) return ps;
     if ((e = cudaMemset(S->state, 0, size_t(NS) * sizeof(SlotState))) != cudaSuccess) return cuda_err(e, "clear");
     if ((e = cudaMemset(S->vis, 0, size_t(NS) * size_t(S->vis_stride) * 4)) != cudaSuccess)
         return cuda_err(e, "clear");
     if ((e = cudaMemset(S->vis_overflow, 0, 4)) != cudaSuccess) return cuda_err(e, "clear");
-    for (int p = 0; p < 2; ++p) {
-        if ((ps = S->halloc(&S->entries[p], size_t(NS))) != PILOT_OK) return ps;
-        if ((ps = S->halloc(&S->n_active[p], 1)) != PILOT_OK) return ps;
-        if ((ps = S->halloc(&S->staging_q[p], size_t(NN) * X.d)) != PILOT_OK) return ps;
-        if ((e = cudaEventCreateWithFlags(&S->step_done[p], cudaEventDisableTiming)) != cudaSuccess)
-            return cuda_err(e, "cudaEventCreate");
-    }
     if ((ps = S->halloc(&S->res_ids, size_t(NS) * c.max_k)) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_dists, size_t(NS) * c.max_k)) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_done, size_t(NS))) != PILOT_OK) return ps;
     if ((ps = S->halloc(&S->res_counters, size_t(NS) * 8)) != PILOT_OK) return ps;
-    if ((e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking)) != cudaSuccess)
-        return cuda_err(e, "cudaStreamCreate");
 
-    // the step graphs (one per parity): reset the slot counter, run the step kernel
+    // the lanes: each its own stream, buffers for the requests it admits and a
+    // step graph (reset the lane's slot counter, run the step kernel)
     ServeIO sio{};
-    sio.next = S->next;
     sio.state = S->state;
     sio.pool = S->pool;
     sio.pool_stride = pool_stride;
     sio.q_pad = S->q_pad;
     sio.qp = S->qp;
-    sio.new_q_pad = S->new_q_pad;
-    sio.new_qp = S->new_qp;
-    sio.new_fes_pos = S->new_pos;
-    sio.new_fes_lb = S->new_lb;
     sio.res_ids = S->res_ids;
     sio.res_dists = S->res_dists;
     sio.res_done = S->res_done;
@@ -435,20 +450,42 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     size_t smem = 0;
     if ((e = prepare_serve_step(XS, S->scfg, S->view.num_sms, NS, &blocks, &smem)) != cudaSuccess)
         return cuda_err(e, "size the step kernel");
-    for (int p = 0; p < 2; ++p) {
-        sio.entries = S->entries[p];
-        sio.n_active = S->n_active[p];
+    S->lanes.resize(size_t(c.streams));
+    for (pilot_server::Lane& L : S->lanes) {
+        if ((ps = S->halloc(&L.entries, size_t(NS))) != PILOT_OK) return ps;
+        if ((ps = S->halloc(&L.n_active, 1)) != PILOT_OK) return ps;
+        if ((ps = S->halloc(&L.staging_q, size_t(NN) * X.d)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.next, 1)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_q, size_t(NN) * X.d)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_q_pad, size_t(NN) * X.d_pad)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_qp, size_t(NN) * X.qp_pad)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_pos, size_t(NN) * S->scfg.fes_T)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_qpb, size_t((NN + 127) / 128 * 128) * X.qp_pad)) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_lb, size_t(NN))) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_bad, size_t(NN))) != PILOT_OK) return ps;
+        if ((ps = S->dalloc(&L.new_status, 8)) != PILOT_OK) return ps;
+        if ((e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_err(e, "cudaEventCreate");
+        if ((e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_err(e, "cudaStreamCreate");
+        sio.entries = L.entries;
+        sio.n_active = L.n_active;
+        sio.next = L.next;
+        sio.new_q_pad = L.new_q_pad;
+        sio.new_qp = L.new_qp;
+        sio.new_fes_pos = L.new_pos;
+        sio.new_fes_lb = L.new_lb;
         cudaGraph_t g = nullptr;
-        if ((e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        if ((e = cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cuda_err(e, "begin capture");
-        cudaError_t e1 = cudaMemsetAsync(S->next, 0, 4, S->stream);
-        cudaError_t e2 = launch_serve_step(XS, S->scfg, sio, S->stream, blocks, smem);
-        cudaError_t e3 = cudaStreamEndCapture(S->stream, &g);
+        cudaError_t e1 = cudaMemsetAsync(L.next, 0, 4, L.stream);
+        cudaError_t e2 = launch_serve_step(XS, S->scfg, sio, L.stream, blocks, smem);
+        cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return cuda_err(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "capture step graph");
         }
-        e = cudaGraphInstantiate(&S->graph[p], g, 0);
+        e = cudaGraphInstantiate(&L.graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_err(e, "instantiate step graph");
     }
@@ -484,6 +521,43 @@ pilot_status pilot_serve_submit(pilot_server* s, const float* q, int k, int ef, 
     *ticket = r.ticket;
     s->queue.push_back(std::move(r));
     ++s->submitted;
+    s->cv_work.notify_one();
+    return PILOT_OK;
+}
+
+pilot_status pilot_serve_submit_batch(pilot_server* s, const float* queries, int64_t n, const int32_t* k,
+                                      const int32_t* ef, uint64_t* tickets) {
+    if (!s || n < 0 || (n > 0 && (!queries || !k || !ef || !tickets)))
+        return err(PILOT_EINVAL, "server, queries, k, ef and tickets must not be NULL");
+    for (int64_t i = 0; i < n; ++i) {   // validate everything before queueing anything
+        if (k[i] < 1 || k[i] > s->cfg.max_k)
+            return err(PILOT_EINVAL, "request %lld: k outside [1, max_k = %lld]", (long long)i, s->cfg.max_k);
+        if (ef[i] < k[i] || ef[i] > s->cfg.max_ef)
+            return err(PILOT_EINVAL, "request %lld: ef outside [k, max_ef = %lld]", (long long)i, s->cfg.max_ef);
+        const float* q = queries + i * s->X.d;
+        for (int64_t j = 0; j < s->X.d; ++j)
+            if (!std::isfinite(q[j])) return err(PILOT_EINVAL, "request %lld holds NaN or infinity", (long long)i);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->broken != PILOT_OK) return err(s->broken, "the server stopped after an error");
+    if (int64_t(s->queue.size()) + n > s->cfg.queue_capacity) {
+        s->rejected += uint64_t(n);
+        return err(PILOT_EBUSY, "the request queue cannot take %lld more (%lld waiting)", (long long)n,
+                   (long long)s->queue.size());
+    }
+    const double t = now_ms();
+    if (s->t_first_submit < 0 && n > 0) s->t_first_submit = t;
+    for (int64_t i = 0; i < n; ++i) {
+        Request r;
+        r.ticket = s->next_ticket++;
+        r.k = k[i];
+        r.ef = ef[i];
+        r.t_submit = t;
+        r.q.assign(queries + i * s->X.d, queries + (i + 1) * s->X.d);
+        tickets[i] = r.ticket;
+        s->queue.push_back(std::move(r));
+    }
+    s->submitted += uint64_t(n);
     s->cv_work.notify_one();
     return PILOT_OK;
 }
@@ -525,7 +599,7 @@ pilot_status pilot_serve_stats(pilot_server* s, pilot_serve_statistics* out) {
     out->completed = s->completed;
     out->steps = s->steps;
     out->slots = s->slots;
-    out->in_flight = int32_t(s->active.size());
+    out->in_flight = int32_t(s->in_flight_requests());
     out->queued = int32_t(s->queue.size());
     int32_t ov = 0;   // read without waiting for the step in flight
     if (cudaMemcpy(&ov, s->vis_overflow, 4, cudaMemcpyDeviceToHost) == cudaSuccess) out->visited_overflows = ov;
@@ -553,8 +627,7 @@ void pilot_serve_destroy(pilot_server* s) {
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    cudaStreamSynchronize(s->stream);
-    delete s;
+    delete s;   // synchronises the lanes' streams first
 }
 
 }  // extern "C"

@@ -311,7 +311,7 @@ class pilot_serve_config(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int32), ("max_ef", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("expansions_per_step", ctypes.c_int32), ("max_new_per_step", ctypes.c_int32),
                 ("step_timeout_ms", ctypes.c_int32), ("queue_capacity", ctypes.c_int64),
-                ("hbm_budget_bytes", ctypes.c_int64)]
+                ("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32)]
 
 
 class pilot_serve_statistics(ctypes.Structure):
@@ -326,6 +326,7 @@ _lib.pilot_serve_config_default.argtypes = [ctypes.POINTER(pilot_serve_config)]
 _lib.pilot_serve_config_default.restype = None
 _lib.pilot_serve_create.argtypes = [_P, ctypes.POINTER(pilot_serve_config), ctypes.POINTER(_P)]
 _lib.pilot_serve_submit.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+_lib.pilot_serve_submit_batch.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P]
 _lib.pilot_serve_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P]
 _lib.pilot_serve_wait_ex.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P, _P]
 _lib.pilot_serve_stats.argtypes = [_P, ctypes.POINTER(pilot_serve_statistics)]
@@ -351,6 +352,17 @@ class PilotServer:
         t = ctypes.c_uint64()
         _check(_lib.pilot_serve_submit(self._h, q.ctypes.data, k, ef, ctypes.byref(t)))
         return t.value
+
+    def submit_batch(self, queries, k, ef) -> np.ndarray:
+        """Queue n queries (n x d) with per-query k and ef (arrays or scalars); returns the tickets."""
+        q = np.ascontiguousarray(queries, np.float32)
+        n = q.shape[0]
+        ks = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)))
+        efs = np.ascontiguousarray(np.broadcast_to(np.asarray(ef, np.int32), (n,)))
+        t = np.empty(n, np.uint64)
+        _check(_lib.pilot_serve_submit_batch(self._h, q.ctypes.data, n, ks.ctypes.data, efs.ctypes.data,
+                                             t.ctypes.data))
+        return t
 
     def wait(self, ticket: int, k: int, timeout_ms: int = 60_000, counters: bool = False):
         """(ids, dists) of a ticket, plus its 8 per-stage counters with ``counters``."""
@@ -396,6 +408,10 @@ def pilot_serve_submit(server: PilotServer, query, k: int, ef: int) -> int:
 
 def pilot_serve_wait(server: PilotServer, ticket: int, k: int, timeout_ms: int = 60_000):
     return server.wait(ticket, k, timeout_ms)
+
+
+def pilot_serve_submit_batch(server: PilotServer, queries, k, ef) -> np.ndarray:
+    return server.submit_batch(queries, k, ef)
 
 
 def pilot_serve_wait_ex(server: PilotServer, ticket: int, k: int, timeout_ms: int = 60_000):

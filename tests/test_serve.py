@@ -106,6 +106,33 @@ def test_mixed_k_and_ef_with_arrivals_equal_the_oracle(env):
         srv.destroy()
 
 
+def test_submit_batch_equals_the_oracle(env):
+    """Requests queued with one pilot_serve_submit_batch call (mixed k and ef)
+    return the oracle's results; a batch with one bad request queues nothing."""
+    pilot, g, Q, oi = env
+    rng = np.random.default_rng(23)
+    n_req = 64
+    rows = rng.integers(0, len(Q), n_req)
+    ks = rng.choice([1, 10, 100], size=n_req).astype(np.int32)
+    efs = np.array([int(rng.integers(max(32, k), 513)) for k in ks], np.int32)
+    ref = _oracle_answers(oi, Q, rows, ks, efs)
+    srv = pilot.pilot_serve_create(g, max_ef=512, max_k=100)
+    try:
+        bad_ef = efs.copy()
+        bad_ef[5] = 600
+        with pytest.raises(pilot.PilotError) as e:
+            srv.submit_batch(Q[rows], ks, bad_ef)
+        assert e.value.status == pilot.PILOT_EINVAL
+        assert srv.stats()["submitted"] == 0
+        tickets = srv.submit_batch(Q[rows], ks, efs)
+        assert len(set(tickets.tolist())) == n_req
+        for j in range(n_req):
+            _assert_same(srv.wait(int(tickets[j]), int(ks[j]), counters=True), ref[j], j)
+        assert srv.stats()["completed"] == n_req
+    finally:
+        srv.destroy()
+
+
 def test_batch_search_equals_the_oracle_at_serving_shapes(env):
     """The batch entry point on the same index and (k, ef) mix, for reference."""
     pilot, g, Q, oi = env
