@@ -87,10 +87,16 @@ def load_workload(name: str, n: int | None = None, nq: int | None = None, verbos
     return w, idx, np.ascontiguousarray(Q), gt
 
 
+_BUILT = {}   # in-process cache of workloads too large for the disk cache
+DISK_CACHE_MAX_FLOATS = 500_000_000
+
+
 def _load_full(name: str, n: int | None, verbose: bool):
     import torch
     from paper_2503_21206_b300 import index_build, synth
     w = synth.WORKLOADS[name]
+    if (name, n) in _BUILT:
+        return _BUILT[(name, n)]
     cdir = _cache_dir(name, n)
     if os.path.exists(os.path.join(cdir, "done")):
         idx = index_build.load_index(cdir)
@@ -102,6 +108,9 @@ def _load_full(name: str, n: int | None, verbose: bool):
     gt, _ = index_build.exact_topk(idx.full, Q, w.k, metric=w.metric, device=dev)
     if verbose:
         print(f"[bench] built {name}: index {t1 - t0:.1f}s, ground truth {time.time() - t1:.1f}s", file=sys.stderr)
+    if idx.n * idx.d > DISK_CACHE_MAX_FLOATS:   # too large to write out: keep it for this process only
+        _BUILT[(name, n)] = (w, idx, Q, gt)
+        return w, idx, Q, gt
     os.makedirs(cdir, exist_ok=True)
     index_build.save_index(idx, cdir)
     np.save(os.path.join(cdir, "queries.npy"), Q)
@@ -240,17 +249,21 @@ def cpu_baseline_entry(idx, Q, k, ef) -> dict:
 
 # ------------------------------------------------------------------ arms --
 
-def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, fixed_ef: int = 0, **cfg) -> dict:
+def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, fixed_ef: int = 0, ef_set=None,
+                **cfg) -> dict:
     """Poisson arrivals at `rate` requests/s of n_req requests with k drawn
     from {1, 10, 100} and ef uniform in 32..512 (ef >= k) -- or, with
-    `fixed_ef`, k = 10 and that ef for all -- submitted from this thread as
-    their arrival times pass; returns the server's statistics and
-    recall@min(k, 10) of the answers."""
+    `fixed_ef`, k = 10 and that ef for all; with `ef_set`, k = 10 and ef drawn
+    from the set -- submitted from this thread as their arrival times pass;
+    returns the server's statistics and recall@min(k, 10) of the answers."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     if fixed_ef:
         ks = np.full(n_req, 10)
         efs = np.full(n_req, fixed_ef)
+    elif ef_set:
+        ks = np.full(n_req, 10)
+        efs = rng.choice(np.asarray(ef_set), size=n_req)
     else:
         ks = rng.choice([1, 10, 100], size=n_req)
         efs = np.array([int(rng.integers(max(32, k), 513)) for k in ks])
@@ -282,8 +295,9 @@ def serving_run(pilot, g, Q, gt, rate: float, n_req: int, seed: int = 5, fixed_e
     return {"offered_rate": rate, "requests": n_req, "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
             "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3), "slots": st["slots"],
             "steps": st["steps"], "recall@min(k,10)": round(hits / tot, 5), "mean_ef": float(efs.mean()),
-            "k_mix": "10" if fixed_ef else "1/10/100 uniform",
-            "ef_mix": f"{fixed_ef} for all" if fixed_ef else "uniform 32..512, ef >= k"}
+            "k_mix": "10" if (fixed_ef or ef_set) else "1/10/100 uniform",
+            "ef_mix": (f"{fixed_ef} for all" if fixed_ef else
+                       (f"uniform over {sorted(int(e) for e in ef_set)}" if ef_set else "uniform 32..512, ef >= k"))}
 
 
 def run_reference(args):
@@ -497,6 +511,71 @@ def forms_summary(args) -> dict:
     if "served_qps" in brief.get("bf16", {}) and "plain" in brief:
         res["served_bf16_over_plain_f32_batch"] = round(brief["bf16"]["served_qps"] / brief["plain"]["batch_qps"], 3)
     return res
+
+
+def run_memory_bounded(args):
+    """The memory-bounded configuration: full vectors in pinned host memory,
+    read over the host link by the re-rank and stages (2)(3); the GPU holds
+    the graphs, the subgraph's reduced rows and the entries.  Batch operating
+    points over the workload's ef list (recall@10 against FP64 brute force,
+    QPS, host-link GB/s of full-row bytes), the QPS at the smallest ef
+    reaching recall 0.9 and 0.95, and a Poisson serving run with mixed ef."""
+    import torch
+    from paper_2503_21206_b300 import pilot
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    t0 = time.time()
+    w, idx, Q, gt = load_workload(args.workload, args.n, args.nq)
+    t_build = time.time() - t0
+    t0 = time.time()
+    g = pilot.load_index_data(idx, full_vecs_host=True)
+    t_load = time.time() - t0
+    info = g.info()
+    nq, k = len(Q), w.k
+    stream = torch.cuda.Stream(device=device)
+    qd = torch.from_numpy(Q).to(device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=device)
+    cnt = torch.empty((nq, 8), dtype=torch.int32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    kms = np.zeros(3, np.float32)
+    d_pad = (idx.d + 31) // 32 * 32
+    batch = []
+    for ef in list(w.efs):
+        pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream, counters=cnt, kernel_ms=kms)
+        torch.cuda.synchronize()
+        rec = recall_at_k(ids.cpu().numpy(), gt, k)
+        c = cnt.cpu().numpy().astype(np.float64)
+        host_bytes = float((c[:, 6] + c[:, 3] + c[:, 5]).sum()) * d_pad * 4   # full rows read over the host link
+        step_ms, search_ms = timed_steps(lambda: pilot.pilot_search_ex(g, qd, k, ef, ids, dists, stream,
+                                                                       kernel_ms=kms),
+                                         stream, flush, args.steps, args.warmup, kms)
+        batch.append({"ef": ef, "recall@10": round(rec, 5), "qps": nq / (step_ms / 1000.0),
+                      "search_kernel_ms": search_ms, "host_link_gbs": host_bytes / (search_ms / 1000.0) / 1e9,
+                      "mean_counters": {nm: round(float(c[:, i].mean()), 1) for i, nm in
+                                        enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}})
+        print(json.dumps(batch[-1]), file=sys.stderr, flush=True)
+    at = {}
+    for target in (0.9, 0.95):
+        hit = next((b for b in batch if b["recall@10"] >= target), None)
+        at[str(target)] = None if hit is None else {"ef": hit["ef"], "qps": round(hit["qps"], 1),
+                                                     "recall@10": hit["recall@10"]}
+    ef_set = [e for e in (128, 256) if e in w.efs] or list(w.efs[:2])
+    base_qps = min(b["qps"] for b in batch if b["ef"] in ef_set)
+    rate = 0.6 * base_qps
+    serving = serving_run(pilot, g, Q, gt, rate, int(min(args.serve_requests, max(2000, rate * 6))), ef_set=ef_set,
+                          max_ef=max(ef_set), max_k=k, expansions_per_step=args.serve_budget)
+    line = {"metric": "memory-bounded: QPS at recall@10 0.9 / 0.95 and p99", "unit": "queries/s", "n_gpus": 1,
+            "data": "synthetic", "config": {"workload": args.workload, "n": idx.n, "d": idx.d, "dp": idx.dp,
+                                            "reduced_dtype": idx.reduced_dtype, "nq": nq, "k": k,
+                                            "metric": "ip" if idx.metric else "l2",
+                                            "full_vecs": "pinned host memory, read over the host link",
+                                            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
+            "device_bytes_of_index": info["device_bytes"], "host_bytes_of_full_vectors": int(idx.n) * d_pad * 4,
+            "build_s": round(t_build, 1), "load_s": round(t_load, 1),
+            "qps_at_recall": at, "batch": batch, "serving": serving}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_serve_sweep(args):
@@ -944,6 +1023,9 @@ def main(argv=None):
                     help="the tau/ef analysis: final stage seeded with tau true neighbours + random nodes")
     ap.add_argument("--ablation", action="store_true",
                     help="component ablation (FES seeds, stages on/off) at --ef (default 256)")
+    ap.add_argument("--memory-bounded", action="store_true",
+                    help="the memory-bounded configuration (full vectors in pinned host memory): QPS at recall "
+                         "0.9 / 0.95 and a mixed-ef serving run; e.g. --workload c5_powerlaw_25m_d768 --nq 2000")
     ap.add_argument("--forms", action="store_true",
                     help="compare the reduced-row precision forms and the plain form (one GPU)")
     args = ap.parse_args(argv)
@@ -955,6 +1037,8 @@ def main(argv=None):
         return run_ablation(args)
     if args.serve_sweep:
         return run_serve_sweep(args)
+    if args.memory_bounded:
+        return run_memory_bounded(args)
     if args.tau:
         return run_tau(args)
     if args.sweep_sub:

@@ -56,8 +56,11 @@ enum { PILOT_REDUCED_F32 = 0, PILOT_REDUCED_BF16 = 1, PILOT_REDUCED_FP8_E4M3 = 2
 
 /*
  * Index description (Sec. 3, Fig. 2 (a)-(c); Sec. 4.3).  All pointers are
- * HOST pointers; pilot_index_load copies everything into library-owned device
- * memory, so the caller may free them as soon as the call returns.
+ * HOST pointers, except full_vecs, which may also be a DEVICE pointer of the
+ * current device (the library tells them apart; a base set generated on the
+ * GPU then never needs a host copy besides the library's own).
+ * pilot_index_load copies everything into library-owned memory, so the caller
+ * may free them as soon as the call returns.
  *
  *  graph           n x R int32, full graph, -1 padded
  *  subgraph_mask   n uint8, 1 = node kept by subgraph sampling

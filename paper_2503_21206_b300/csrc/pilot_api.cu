@@ -51,6 +51,24 @@ double decode_e4m3_host(uint8_t c) {
     return (c & 0x80) ? -v : v;
 }
 
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Non-finite values among n floats in device memory (load-time validation of
+// full vectors given as a device pointer).
+__global__ void count_nonfinite_kernel(const float* p, int64_t n, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        c += !isfinite(p[i]);
+    if (c) atomicAdd(out, c);
+}
+
 double decode_bf16_host(uint16_t h) {
     uint32_t b = uint32_t(h) << 16;
     float f;
@@ -100,15 +118,22 @@ struct pilot_index {
     // rows x width elements of esize bytes into rows x pitch_bytes, zero padded
     // Rows copied into pinned host memory mapped into the device's address
     // space; *out is the device-side address.
-    pilot_status map_rows(const void* host, int64_t rows, size_t width_bytes, size_t pitch_bytes, const void** out) {
+    pilot_status map_rows(const void* src, int64_t rows, size_t width_bytes, size_t pitch_bytes, bool src_dev,
+                          const void** out) {
         void* h = nullptr;
         size_t bytes = std::max<size_t>(size_t(rows) * pitch_bytes, 16);
         CUDA_TRY(cudaHostAlloc(&h, bytes, cudaHostAllocMapped));
         host_allocs.push_back(h);
-        std::memset(h, 0, bytes);
-        for (int64_t r = 0; r < rows; ++r)
-            std::memcpy(static_cast<char*>(h) + size_t(r) * pitch_bytes,
-                        static_cast<const char*>(host) + size_t(r) * width_bytes, width_bytes);
+        if (pitch_bytes != width_bytes) std::memset(h, 0, bytes);
+        if (src_dev) {   // straight from device memory into the pinned rows
+            if (rows)
+                CUDA_TRY(cudaMemcpy2D(h, pitch_bytes, src, width_bytes, width_bytes, size_t(rows),
+                                      cudaMemcpyDeviceToHost));
+        } else {
+            for (int64_t r = 0; r < rows; ++r)
+                std::memcpy(static_cast<char*>(h) + size_t(r) * pitch_bytes,
+                            static_cast<const char*>(src) + size_t(r) * width_bytes, width_bytes);
+        }
         void* d = nullptr;
         CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
         *out = d;
@@ -124,8 +149,7 @@ struct pilot_index {
         device_bytes += bytes;
         if (pitch_bytes != width_bytes) CUDA_TRY(cudaMemset(p, 0, bytes));
         if (rows)
-            CUDA_TRY(cudaMemcpy2D(p, pitch_bytes, host, width_bytes, width_bytes, size_t(rows),
-                                  cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy2D(p, pitch_bytes, host, width_bytes, width_bytes, size_t(rows), cudaMemcpyDefault));
         *out = p;
         return PILOT_OK;
     }
@@ -251,8 +275,28 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
         if (v < 0 || v >= n || !D.subgraph_mask[v])
             return fail(PILOT_EINVAL, "entry %lld (id %d) is not a sampled node", (long long)e, v);
     }
-    for (int64_t i = 0; i < n * d; ++i)
-        if (!std::isfinite(D.full_vecs[i])) return fail(PILOT_EINVAL, "full_vecs holds a non-finite value");
+    // full vectors may be given in device memory (of the current device)
+    const bool full_dev = is_device_ptr(D.full_vecs);
+    if (full_dev) {
+        unsigned long long* cnt = nullptr;
+        unsigned long long bad = 0;
+        int dev = 0, sms = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CUDA_TRY(cudaMalloc(&cnt, sizeof bad));
+        cudaError_t e1 = cudaMemset(cnt, 0, sizeof bad);
+        if (e1 == cudaSuccess) {
+            count_nonfinite_kernel<<<unsigned(sms * 8), 256>>>(D.full_vecs, n * d, cnt);
+            e1 = cudaGetLastError();
+        }
+        if (e1 == cudaSuccess) e1 = cudaMemcpy(&bad, cnt, sizeof bad, cudaMemcpyDeviceToHost);
+        cudaFree(cnt);
+        CUDA_TRY(e1);
+        if (bad) return fail(PILOT_EINVAL, "full_vecs holds a non-finite value");
+    } else {
+        for (int64_t i = 0; i < n * d; ++i)
+            if (!std::isfinite(D.full_vecs[i])) return fail(PILOT_EINVAL, "full_vecs holds a non-finite value");
+    }
     for (int64_t i = 0; i < d * dp; ++i)
         if (!std::isfinite(D.svd_basis[i])) return fail(PILOT_EINVAL, "svd_basis holds a non-finite value");
 
@@ -375,7 +419,8 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     X.red = p;
     X.full_host = D.full_vecs_location == PILOT_FULL_VECS_HOST;
     if (X.full_host) {
-        if ((s = ix->map_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) return s;
+        if ((s = ix->map_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), full_dev, &p)) != PILOT_OK)
+            return s;
     } else if ((s = ix->upload_rows(D.full_vecs, n, size_t(d * 4), size_t(X.full_row_bytes), &p)) != PILOT_OK) {
         return s;
     }
@@ -509,14 +554,6 @@ pilot_status pilot_index_load_files(const char* dir, int flags, pilot_index** ou
     return pilot_index_load(&D, out);
 }
 
-static bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 

@@ -298,18 +298,20 @@ __device__ __forceinline__ void approx_chunk(float& a0, float& a1, float& b, uin
     }
 }
 
-// Keep flags of staged rows 0..m-1: w.sel[i] = 0 when row i's certified
-// lower bound exceeds thr (it cannot enter C), else 1.  One row per lane:
-// lane i sums its whole row (the staging stride keeps the lanes' chunks in
-// distinct banks), so no shuffle is needed; cand[cand_off + i] is row i's id
-// (for the FP8 scale).  The caller synchronises the warp afterwards.
-template <int DT, int METRIC>
+// Keep flags of staged rows rows(0..m-1): w.sel[i] = 0 when row rows(i)'s
+// certified lower bound exceeds thr (it cannot enter C), else 1.  One row per
+// lane: lane i sums its whole row (the staging stride keeps the lanes' chunks
+// in distinct banks), so no shuffle is needed; cand[cand_off + row] is the
+// row's id (for the FP8 scale).  The caller synchronises the warp afterwards.
+template <int DT, int METRIC, class Rows>
 __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float* __restrict__ scales,
-                                            const float* q, int m, int cand_off, int n_elems, float thr) {
+                                            const float* q, int m, int cand_off, int n_elems, float thr,
+                                            Rows rows) {
     const int i = w.lane;
     if (i >= m) return;
     constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
-    const uint8_t* rowp = w.stage + i * stage_stride(row_bytes);
+    const int row = rows(i);   // the staged row lane i tests
+    const uint8_t* rowp = w.stage + row * stage_stride(row_bytes);
     const int nch = row_bytes >> 4;
     float a0 = 0.0f, a1 = 0.0f, b = 0.0f;
 #pragma unroll 2
@@ -321,7 +323,7 @@ __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float*
     if (METRIC == 0) {
         lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
     } else if (DT == 2) {
-        const float sc = __ldg(scales + w.cand[cand_off + i]);
+        const float sc = __ldg(scales + w.cand[cand_off + row]);
         lb = __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
     } else {
         lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
@@ -372,17 +374,58 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
 // issues one bulk copy of row r0 + i; all complete on the warp's mbarrier.
 // Rows in host memory mapped into the device's address space (`plain`) are
 // copied instead with 16-byte loads spread over all lanes.
+// Rows in pinned host memory mapped into the device's address space: 16-byte
+// loads spread over the lanes, 4 independent loads in flight per lane before
+// any is stored (the host link's latency is what this waits on; more would
+// push the kernel's register allocation past 128 and spill).
 __device__ __noinline__ void gather_rows_plain(uint8_t* stage, const uint8_t* __restrict__ base, int row_bytes,
                                               const int32_t* cand, int n, int lane) {
+    constexpr int kInFlight = 4;
     const int cpr = row_bytes >> 4;
     const int total = n * cpr;
     __syncwarp();
-#pragma unroll 4
-    for (int c = lane; c < total; c += 32) {
-        const int r = c / cpr, o = c - r * cpr;
-        const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(cand[r]) * row_bytes + o * 16);
-        *reinterpret_cast<uint4*>(stage + r * stage_stride(row_bytes) + o * 16) = v;
+    for (int c0 = lane; c0 < total; c0 += 32 * kInFlight) {
+        uint4 v[kInFlight];
+#pragma unroll
+        for (int u = 0; u < kInFlight; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < total) {
+                const int r = c / cpr, o = c - r * cpr;
+                v[u] = *reinterpret_cast<const uint4*>(base + int64_t(cand[r]) * row_bytes + o * 16);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kInFlight; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < total) {
+                const int r = c / cpr, o = c - r * cpr;
+                *reinterpret_cast<uint4*>(stage + r * stage_stride(row_bytes) + o * 16) = v[u];
+            }
+        }
     }
+    __syncwarp();
+}
+
+// Issue one bulk copy per row for rows cand[r0 .. r0+n) (n <= 32) into the
+// staging buffer, all completing on the warp's mbarrier; gather_wait waits.
+__device__ __forceinline__ void gather_issue(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int r0,
+                                             int n) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
+    __syncwarp();
+    if (w.lane < n)
+        bulk_copy_g2s(w.stage + w.lane * stage_stride(row_bytes), base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
+                      uint32_t(row_bytes), w.bar);
+}
+
+__device__ __forceinline__ void gather_wait(Warp& w) {
+    if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
+        // give the copies still in flight one more bounded wait, then report
+        mbar_wait(w.bar, w.phase, kMaxPolls);
+        w.failed = true;
+    }
+    w.phase ^= 1u;
     __syncwarp();
 }
 
@@ -393,20 +436,8 @@ __device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__
         gather_rows_plain(w.stage, base, row_bytes, w.cand + r0, n, w.lane);
         return;
     }
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
-    __syncwarp();
-    if (w.lane < n)
-        bulk_copy_g2s(w.stage + w.lane * stage_stride(row_bytes), base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
-                      uint32_t(row_bytes), w.bar);
-    if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
-        // give the copies still in flight one more bounded wait, then report
-        mbar_wait(w.bar, w.phase, kMaxPolls);
-        w.failed = true;
-    }
-    w.phase ^= 1u;
-    __syncwarp();
+    gather_issue(w, base, row_bytes, r0, n);
+    gather_wait(w);
 }
 
 // Exact distances of rows cand[0..m) of a row array (`base`, `row_bytes` per
@@ -442,7 +473,7 @@ __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict
         gather_rows(w, base, row_bytes, r0, r1, plain);
         bool keep = w.lane < nr;
         if (filter) {
-            approx_keep<DT, METRIC>(w, row_bytes, scales, q, nr, r0, n_elems, thr);
+            approx_keep<DT, METRIC>(w, row_bytes, scales, q, nr, r0, n_elems, thr, [](int i) { return i; });
             __syncwarp();
             keep = keep && w.sel[w.lane] != 0;
             __syncwarp();
@@ -645,14 +676,18 @@ struct Searcher {
         const int32_t* row = adjacency(view, u);
         const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
         // the next expansion most likely takes the second unchecked candidate:
-        // read its adjacency row now (the load completes while this expansion
-        // probes), then bring its neighbours' visited-table buckets into L2, so
-        // that the next probe mostly hits L2
-        int32_t ahead = -1;
+        // bring its adjacency row (every 128-byte line it spans) into L2 while
+        // this one runs (prefetching its neighbours' visited buckets as well
+        // cost more DRAM traffic than it saved: the guess is wrong about 40%
+        // of the time)
         if (idx2 >= 0) {
             const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
-            const int W2 = view == 3 ? ix.R : ix.R_sub;
-            if (r2 && lane < W2) ahead = __ldg(r2 + lane);
+            if (r2) {
+                const uintptr_t first = reinterpret_cast<uintptr_t>(r2) >> 7;
+                const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + (view == 3 ? ix.R : ix.R_sub)) - 1) >> 7;
+                if (uintptr_t(lane) <= last - first)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"((first + lane) << 7));
+            }
         }
         __syncwarp();
         for (int b0 = 0; b0 < W; b0 += 32) {
@@ -664,17 +699,12 @@ struct Searcher {
             // the visited probe comes first: only unvisited neighbours are
             // gathered and scored
             const bool isnew = visit(w, v, v >= 0);
-            // the look-ahead row has arrived by now: prefetch its buckets so that
-            // they travel while this expansion scores its rows (stage (2)'s rows
-            // hold compact ids; it runs only 2 expansions)
-            if (b0 == 0 && view != 2 && ahead >= 0)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(w.vis + size_t(vis_bucket(w, ahead)) * kVisBucket));
             const unsigned nb = __ballot_sync(kFull, isnew);
             const int m = __popc(nb);
-            n_dist += m;
-            if (m == 0) continue;
             if (isnew) w.cand[__popc(nb & lanemask_lt())] = v;
             __syncwarp();
+            n_dist += m;
+            if (m == 0) continue;
             // a full list only admits keys below its worst one: rows certified
             // above its distance are not scored exactly
             const bool full = w.S == w.ef;
@@ -1106,8 +1136,9 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
 }
 
 template <int DT, int METRIC>
-cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,
+cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const SearchIO& io, cudaStream_t st,
                      int num_sms) {
+    const SearchConfig& cfg = cfg_in;
     const Layout L = make_layout(ix, cfg);
     const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
     int dev = 0, smem_max = 0;
@@ -1156,8 +1187,9 @@ cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num
 }
 
 template <int DT, int METRIC>
-cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
+cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const ServeIO& sio, cudaStream_t st,
                            int blocks, size_t smem) {
+    const SearchConfig& cfg = cfg_in;
     serve_step_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, sio,
                                                                                            make_layout(ix, cfg));
     return cudaGetLastError();

@@ -2,9 +2,10 @@
 
 Builds, from a base set X, every input the search reads:
 
-* the full graph (a): exact 2R-nearest candidates, the HNSW neighbour-selection
-  heuristic to R, reverse edges, re-selection, and a reachability repair from
-  the entry set so that every node can be reached;
+* the full graph (a): the 2R nearest candidates (exact up to 3M rows, from
+  inverted lists beyond), the HNSW neighbour-selection heuristic to R, reverse
+  edges, re-selection, and a reachability repair from the entry set so that
+  every node can be reached;
 * the subgraph (b): a seeded uniform node sample, re-connected by the same
   construction among the sampled nodes, stored in the full id space with
   zero-degree rows for unsampled nodes (Sec. 4.3);
@@ -29,6 +30,7 @@ import torch
 from .synth import Workload
 
 DTYPE_CODES = {"f32": 0, "bf16": 1, "fp8": 2}
+IVF_ABOVE = 3_000_000   # graph candidates by inverted lists above this many rows
 FILE_MAGIC = "pilot-index 1"
 
 
@@ -42,7 +44,7 @@ class PilotIndexData:
     reduced: np.ndarray          # n_sub x dp: float32 | uint16 (bf16 bits) | uint8 (e4m3 codes)
     reduced_dtype: str           # "f32" | "bf16" | "fp8"
     reduced_scales: np.ndarray | None   # n_sub float32 (fp8)
-    full: np.ndarray             # n x d float32
+    full: np.ndarray             # n x d float32 (a CUDA tensor for a base set drawn on the GPU)
     entry_ids: np.ndarray        # n_entry int32
     metric: int                  # 0 L2, 1 IP
     entry_cluster: np.ndarray | None = None       # n_entry int32: coarse cluster of each entry (clustered FES)
@@ -73,11 +75,25 @@ def _dev(device):
     return torch.device(device if device is not None else "cpu")
 
 
+def _as_tensor(X, dev):
+    """X (numpy array, or a float32 torch tensor already on a device) as an FP32 tensor on dev."""
+    if torch.is_tensor(X):
+        return X.to(dev, torch.float32)
+    return torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+
+
+def _rows(X, idx: np.ndarray) -> np.ndarray:
+    """Rows idx of X as a host FP32 array (X numpy or a torch tensor)."""
+    if torch.is_tensor(X):
+        return X[torch.from_numpy(np.asarray(idx, np.int64)).to(X.device)].float().cpu().numpy()
+    return np.asarray(X[idx], np.float32)
+
+
 def knn_candidates(X: np.ndarray, k: int, device=None, chunk: int = 4096, exclude_self: bool = True):
     """Exact k nearest neighbours of every row of X among the rows of X by
     squared L2 (FP32), ordered by (distance, id).  Returns (ids, dists)."""
     dev = _dev(device)
-    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    Xt = _as_tensor(X, dev)
     n = Xt.shape[0]
     norms = (Xt.double() ** 2).sum(1).float()
     k_eff = min(k, n - 1 if exclude_self else n)
@@ -102,6 +118,86 @@ def knn_candidates(X: np.ndarray, k: int, device=None, chunk: int = 4096, exclud
         ex, idx = torch.gather(ex, 1, o2), torch.gather(idx, 1, o2)
         ids[s:e] = idx[:, :k_eff]
         dst[s:e] = ex[:, :k_eff]
+    return ids, dst
+
+
+def ivf_candidates(X: np.ndarray, k: int, device=None, nlist: int | None = None, nprobe: int = 8, seed: int = 0,
+                   iters: int = 10, verbose: bool = False):
+    """Approximate k nearest neighbours of every row of X among the rows of X
+    (squared L2), for base sets too large for the exact quadratic search.
+
+    The rows are split into nlist inverted lists by k-means (a seeded sample,
+    Lloyd iterations); the rows of each list are scored (FP32 matrix product)
+    against every row of the nprobe lists whose centroids are closest to the
+    list's own, the best k + 8 are rescored exactly in FP32, and the first k
+    by (distance, id) are kept.  Returns (ids, dists) like knn_candidates; a
+    row whose probed lists hold fewer than k others gets -1 / +inf padding."""
+    dev = _dev(device)
+    Xt = _as_tensor(X, dev)
+    n, d = Xt.shape
+    if nlist is None:
+        nlist = int(min(16384, max(16, n // 2048)))
+    nprobe = min(nprobe, nlist)
+    rng = np.random.default_rng(seed)
+    norms = (Xt * Xt).sum(1)
+
+    def nearest(A, C, Cn, chunk=65536):
+        out = torch.empty(A.shape[0], dtype=torch.int64, device=dev)
+        for s in range(0, A.shape[0], chunk):
+            a = A[s:s + chunk]
+            out[s:s + chunk] = torch.argmin(Cn[None, :] - 2.0 * (a @ C.T), dim=1)
+        return out
+
+    # k-means on a sample
+    samp = torch.from_numpy(np.sort(rng.choice(n, size=min(n, 64 * nlist), replace=False))).to(dev)
+    Xs = Xt[samp]
+    C = Xs[torch.from_numpy(rng.choice(Xs.shape[0], size=nlist, replace=False)).to(dev)].clone()
+    for it in range(iters):
+        lab = nearest(Xs, C, (C * C).sum(1))
+        cnt = torch.bincount(lab, minlength=nlist).float()
+        Cs = torch.zeros_like(C).index_add_(0, lab, Xs)
+        ok = cnt > 0
+        C[ok] = Cs[ok] / cnt[ok, None]
+    labels = nearest(Xt, C, (C * C).sum(1))
+    order = torch.argsort(labels, stable=True)
+    counts = torch.bincount(labels, minlength=nlist)
+    offs = torch.cat([torch.zeros(1, dtype=torch.int64, device=dev), torch.cumsum(counts, 0)]).cpu().numpy()
+    Cn = (C * C).sum(1)
+    Dcc = Cn[:, None] + Cn[None, :] - 2.0 * (C @ C.T)
+    Dcc.fill_diagonal_(-float("inf"))           # each list probes itself first
+    probe = torch.topk(Dcc, nprobe, dim=1, largest=False).indices.cpu().numpy()
+    order_np = order.cpu().numpy()
+    ids = torch.full((n, k), -1, dtype=torch.int64, device=dev)
+    dst = torch.full((n, k), float("inf"), dtype=torch.float32, device=dev)
+    kk = k + 8
+    qchunk = 4096
+    for L in range(nlist):
+        if offs[L + 1] == offs[L]:
+            continue
+        q_ids = order[offs[L]:offs[L + 1]]
+        pool = torch.cat([order[offs[c]:offs[c + 1]] for c in probe[L]])
+        Xp = Xt[pool]
+        pn = norms[pool]
+        for s in range(0, q_ids.numel(), qchunk):
+            qi = q_ids[s:s + qchunk]
+            Xq = Xt[qi]
+            D = norms[qi][:, None] + pn[None, :] - 2.0 * (Xq @ Xp.T)
+            D[torch.arange(qi.numel(), device=dev), torch.arange(s, s + qi.numel(), device=dev)] = float("inf")
+            kc = min(kk, pool.numel())
+            _, sel = torch.topk(D, kc, dim=1, largest=False)
+            cand = pool[sel]
+            ex = ((Xq[:, None, :] - Xt[cand]) ** 2).sum(-1)
+            ex = torch.where(cand == qi[:, None], torch.full_like(ex, float("inf")), ex)
+            o1 = torch.argsort(cand, dim=1, stable=True)
+            ex, cand = torch.gather(ex, 1, o1), torch.gather(cand, 1, o1)
+            o2 = torch.argsort(ex, dim=1, stable=True)
+            ex, cand = torch.gather(ex, 1, o2), torch.gather(cand, 1, o2)
+            kt = min(k, kc)
+            ok = torch.isfinite(ex[:, :kt])
+            ids[qi, :kt] = torch.where(ok, cand[:, :kt], torch.full_like(cand[:, :kt], -1))
+            dst[qi, :kt] = ex[:, :kt]
+        if verbose and L % 1024 == 0:
+            print(f"ivf candidates: list {L}/{nlist}", flush=True)
     return ids, dst
 
 
@@ -139,14 +235,23 @@ def select_neighbours(Xt: torch.Tensor, node: torch.Tensor, cand: torch.Tensor, 
     return torch.where(kept, out, torch.full_like(out, -1))
 
 
-def build_graph(X: np.ndarray, R: int, entries_local: np.ndarray, device=None, chunk: int = 16384,
-                verbose: bool = False) -> np.ndarray:
-    """Out-degree-R graph over the rows of X (local ids), -1 padded."""
+def build_graph(X: np.ndarray, R: int, entries_local: np.ndarray, device=None, chunk: int = 0,
+                verbose: bool = False, candidates: str = "exact", seed: int = 0) -> np.ndarray:
+    """Out-degree-R graph over the rows of X (local ids), -1 padded.
+    ``candidates``: "exact" (the 2R nearest) or "ivf" (ivf_candidates, for
+    base sets too large for the exact search).  Rows are processed ``chunk``
+    at a time (default: as many as keep each chunk's 3R candidate rows near
+    8 GB, at least 16384)."""
     dev = _dev(device)
-    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    Xt = _as_tensor(X, dev)
     n = Xt.shape[0]
+    if chunk <= 0:
+        chunk = int(max(16384, min(65536, 8e9 // (3 * R * Xt.shape[1] * 4))))
     C = min(2 * R, n - 1)
-    cand, cd = knn_candidates(X, C, device=device)
+    if candidates == "ivf":
+        cand, cd = ivf_candidates(X, C, device=device, seed=seed, verbose=verbose)
+    else:
+        cand, cd = knn_candidates(X, C, device=device)
     adj = torch.full((n, R), -1, dtype=torch.int64, device=dev)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
@@ -156,7 +261,9 @@ def build_graph(X: np.ndarray, R: int, entries_local: np.ndarray, device=None, c
     src = torch.arange(n, device=dev)[:, None].expand(n, R)
     m = adj >= 0
     es, ed = src[m], adj[m]
-    edist = ((Xt[es] - Xt[ed]) ** 2).sum(-1)
+    edist = torch.empty(es.numel(), dtype=torch.float32, device=dev)
+    for a in range(0, es.numel(), 1 << 22):   # in chunks: n x R x d floats would not fit at 10M+ rows
+        edist[a:a + (1 << 22)] = ((Xt[es[a:a + (1 << 22)]] - Xt[ed[a:a + (1 << 22)]]) ** 2).sum(-1)
     o = torch.argsort(edist, stable=True)
     es, ed, edist = es[o], ed[o], edist[o]
     o = torch.argsort(ed, stable=True)
@@ -205,17 +312,19 @@ def _reached_from(adj: np.ndarray, sources: np.ndarray) -> np.ndarray:
 
 
 def repair_reachability(X: np.ndarray, adj: np.ndarray, sources: np.ndarray, device=None,
-                        verbose: bool = False, max_rounds: int = 10_000) -> int:
+                        verbose: bool = False, max_rounds: int = 10_000, max_targets: int = 1 << 20) -> int:
     """Make every node reachable from ``sources`` (in place).
 
     Each round links every unreached node that no other unreached node points
     to (or, if none, the unreached node closest to the reached set -- one per
     weakly connected group of unreached nodes when more than 16 such groups
     remain, so that an index of many separate clusters does not take a round
-    per cluster) from its nearest reached node with a free adjacency slot.
+    per cluster) from its nearest reached node with a free adjacency slot
+    (nearest among a seeded sample of max_targets such nodes when there are
+    more).
     Returns edges added."""
     dev = _dev(device)
-    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    Xt = _as_tensor(X, dev)
     n, R = adj.shape
     added = 0
     for _ in range(max_rounds):
@@ -234,14 +343,17 @@ def repair_reachability(X: np.ndarray, adj: np.ndarray, sources: np.ndarray, dev
         F = np.nonzero(free)[0]
         if F.size == 0:
             F = np.nonzero(reached)[0]
+        if F.size > max_targets:   # a seeded sample of the candidate targets (large base sets)
+            F = np.sort(np.random.default_rng(F.size).choice(F, size=max_targets, replace=False))
         pick = S if S.size else U
         Xs = Xt[torch.from_numpy(pick).to(dev)]
         Xf = Xt[torch.from_numpy(F).to(dev)]
         kk = min(8, F.size)
         best_d = []
         best_i = []
+        fn = (Xf ** 2).sum(1)
         for s in range(0, Xs.shape[0], 2048):
-            D = (Xs[s:s + 2048] ** 2).sum(1)[:, None] - 2 * Xs[s:s + 2048] @ Xf.T + (Xf ** 2).sum(1)[None, :]
+            D = (Xs[s:s + 2048] ** 2).sum(1)[:, None] - 2 * Xs[s:s + 2048] @ Xf.T + fn[None, :]
             v, i = torch.topk(D, kk, dim=1, largest=False)
             best_d.append(v.cpu())
             best_i.append(i.cpu())
@@ -291,7 +403,7 @@ def svd_basis(X: np.ndarray, seed: int, max_rows: int = 262_144) -> np.ndarray:
     rng = np.random.default_rng(seed)
     n = X.shape[0]
     rows = np.sort(rng.choice(n, size=min(n, max_rows), replace=False))
-    A = X[rows].astype(np.float64)
+    A = _rows(X, rows).astype(np.float64)
     _, _, vt = np.linalg.svd(A, full_matrices=False)
     V = vt.T.copy()
     if V.shape[1] < X.shape[1]:   # fewer rows than columns: complete the basis
@@ -303,8 +415,13 @@ def svd_basis(X: np.ndarray, seed: int, max_rows: int = 262_144) -> np.ndarray:
 
 
 def project_rows(X: np.ndarray, basis: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
-    """x V[:, :dp] in FP64, rounded to FP32."""
+    """x V[:, :dp] in FP64, rounded to FP32 (X numpy, or a torch tensor: then on its device)."""
     out = np.empty((X.shape[0], basis.shape[1]), np.float32)
+    if torch.is_tensor(X):
+        Vt = torch.from_numpy(basis).to(X.device)
+        for s in range(0, X.shape[0], chunk):
+            out[s:s + chunk] = (X[s:s + chunk].double() @ Vt).float().cpu().numpy()
+        return out
     for s in range(0, X.shape[0], chunk):
         out[s:s + chunk] = (X[s:s + chunk].astype(np.float64) @ basis).astype(np.float32)
     return out
@@ -383,8 +500,13 @@ def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int,
     entry_local = np.sort(erng.choice(n_sub, size=n_entry, replace=False))
     entry_ids = sampled[entry_local].astype(np.int32)
 
-    graph = build_graph(X, R, entry_ids, device=device, verbose=verbose)
-    sub_local = build_graph(X[sampled], R_sub, entry_local, device=device, verbose=verbose)
+    # exact candidates up to 3M rows; inverted-list candidates beyond (the
+    # exact search is quadratic in n)
+    cands = "exact" if n <= IVF_ABOVE else "ivf"
+    graph = build_graph(X, R, entry_ids, device=device, verbose=verbose, candidates=cands, seed=seed_graph)
+    Xs = X[torch.from_numpy(sampled).to(X.device)] if torch.is_tensor(X) else X[sampled]
+    sub_local = build_graph(Xs, R_sub, entry_local, device=device, verbose=verbose,
+                            candidates="exact" if n_sub <= IVF_ABOVE else "ivf", seed=seed_graph + 1)
     subgraph = np.full((n, R_sub), -1, np.int32)
     subgraph[sampled] = np.where(sub_local >= 0, sampled[np.maximum(sub_local, 0)], -1).astype(np.int32)
     mask = np.zeros(n, np.uint8)
@@ -392,12 +514,14 @@ def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int,
 
     V = svd_basis(X, seed_graph)
     basis = np.ascontiguousarray(V[:, :dp])
-    red32 = project_rows(X[sampled], basis)
+    red32 = project_rows(Xs, basis)
+    del Xs
     red, scales = quantize_rows(red32, reduced_dtype)
     # coarse clusters of the entry set for the clustered FES (r = 32, Sec. 5)
     ent_cluster, centroids = cluster_entries(red32[entry_local], 32, seed_entry)
+    full = X if torch.is_tensor(X) else np.ascontiguousarray(X, np.float32)   # a device base set stays there
     idx = PilotIndexData(graph, mask, subgraph, basis, red, reduced_dtype, scales,
-                         np.ascontiguousarray(X, np.float32), entry_ids, metric, ent_cluster, centroids)
+                         full, entry_ids, metric, ent_cluster, centroids)
     if keep_reduced_f32:
         return idx, red32, V
     return idx
@@ -405,9 +529,15 @@ def build_index(X: np.ndarray, R: int, R_sub: int, sample_ratio: float, dp: int,
 
 def build_workload(w: Workload, device=None, n: int | None = None, nq: int | None = None,
                    reduced_dtype: str | None = None, verbose: bool = False):
-    """(index, queries, reduced FP32 rows, full basis V) for a workload."""
-    from .synth import generate
-    X, Q = generate(w, n=n, nq=nq)
+    """(index, queries, reduced FP32 rows, full basis V) for a workload.  A
+    workload marked ``device_base`` (the 25M x 768 one) draws its base set on
+    the GPU and keeps it there: ``index.full`` is then a CUDA tensor."""
+    from .synth import generate, generate_base_on_device
+    if w.extra.get("device_base") and device is not None and str(device).startswith("cuda"):
+        X = generate_base_on_device(w, n=n, device=device)
+        _, Q = generate(w, n=0, nq=nq)
+    else:
+        X, Q = generate(w, n=n, nq=nq)
     rd = reduced_dtype or w.reduced_dtypes[0]
     idx, red32, V = build_index(X, w.R, w.R_sub, w.sample_ratio, w.dp, w.n_entry, w.metric, w.graph_seed,
                                 w.entry_seed, rd, device=device, verbose=verbose, keep_reduced_f32=True)
@@ -492,13 +622,23 @@ def exact_topk(X: np.ndarray, Q: np.ndarray, k: int, metric: int = 0, device=Non
     score, less a bound on the FP32 error, exceeds the k-th FP64 distance;
     uncertified queries are recomputed over all rows in FP64."""
     dev = _dev(device)
-    Xt = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    Xt = _as_tensor(X, dev)
     xn = (Xt.double() ** 2).sum(1)
     n, d = X.shape
     kk = min(k + margin, n)
     ids_out = np.empty((Q.shape[0], k), np.int32)
     d_out = np.empty((Q.shape[0], k), np.float64)
-    X64 = X.astype(np.float64) if n * d <= 50_000_000 else None
+    X64 = None if torch.is_tensor(X) or n * d > 50_000_000 else X.astype(np.float64)
+    chunk = max(16, min(chunk, int(2_000_000_000 // n)))   # score matrix <= ~8 GB
+
+    def full_fp64(q64):   # every row's FP64 distance, in row chunks on the device
+        qt = torch.from_numpy(q64).to(dev)
+        out = np.empty(n, np.float64)
+        for r in range(0, n, 1 << 20):
+            xr = Xt[r:r + (1 << 20)].double()
+            out[r:r + xr.shape[0]] = (((xr - qt) ** 2).sum(1) if metric == 0 else -(xr @ qt)).cpu().numpy()
+        return out
+
     for s in range(0, Q.shape[0], chunk):
         Qt = torch.from_numpy(np.ascontiguousarray(Q[s:s + chunk], np.float32)).to(dev)
         ip = Qt @ Xt.T
@@ -510,7 +650,10 @@ def exact_topk(X: np.ndarray, Q: np.ndarray, k: int, metric: int = 0, device=Non
         vals, idx = torch.topk(score, kk, dim=1, largest=False)
         vals, idx = vals.cpu().numpy().astype(np.float64), idx.cpu().numpy()
         q64 = Q[s:s + chunk].astype(np.float64)
-        xc = X[idx].astype(np.float64)
+        if torch.is_tensor(X):
+            xc = Xt[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        else:
+            xc = X[idx].astype(np.float64)
         if metric == 0:
             ex = ((q64[:, None, :] - xc) ** 2).sum(-1)
         else:
@@ -523,8 +666,10 @@ def exact_topk(X: np.ndarray, Q: np.ndarray, k: int, metric: int = 0, device=Non
             top_ids, top_d = idx[i][order][:k], ex[i][order][:k]
             if kk < n and not (vals[i, -1] - bound[i] > top_d[-1]):
                 # not certified: exact FP64 over every row
-                xr = X64 if X64 is not None else X.astype(np.float64)
-                full = ((q64[i] - xr) ** 2).sum(1) if metric == 0 else -(xr @ q64[i])
+                if X64 is not None:
+                    full = ((q64[i] - X64) ** 2).sum(1) if metric == 0 else -(X64 @ q64[i])
+                else:
+                    full = full_fp64(q64[i])
                 o = np.lexsort((np.arange(n), full))[:k]
                 top_ids, top_d = o, full[o]
             ids_out[s + i] = top_ids

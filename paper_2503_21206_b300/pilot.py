@@ -178,11 +178,17 @@ def pilot_index_load(graph, subgraph_mask, subgraph, svd_basis, reduced_vecs, fu
     """Copy an index (host numpy arrays, layouts as in pilot.h) to the current device.
     ``full_vecs_host`` keeps the full vectors in pinned host memory instead;
     ``entry_cluster`` / ``cluster_centroids`` enable the clustered FES."""
+    if _device_of(full_vecs) is not None:   # a CUDA tensor: the library copies from device memory
+        if _dtype_name(full_vecs) != "float32" or len(full_vecs.shape) != 2 or not full_vecs.is_contiguous():
+            raise ValueError("full_vecs on the device must be a contiguous float32 (n, d) tensor")
+        fv = full_vecs
+    else:
+        fv = np.ascontiguousarray(full_vecs, np.float32)
     arrs = dict(graph=np.ascontiguousarray(graph, np.int32), subgraph_mask=np.ascontiguousarray(subgraph_mask, np.uint8),
                 subgraph=np.ascontiguousarray(subgraph, np.int32),
                 svd_basis=np.ascontiguousarray(svd_basis, np.float64),
                 reduced_vecs=np.ascontiguousarray(reduced_vecs),
-                full_vecs=np.ascontiguousarray(full_vecs, np.float32),
+                full_vecs=fv,
                 entry_ids=np.ascontiguousarray(entry_ids, np.int32))
     sc = None if reduced_scales is None else np.ascontiguousarray(reduced_scales, np.float32)
     ec = None if entry_cluster is None else np.ascontiguousarray(entry_cluster, np.int32)

@@ -53,8 +53,8 @@ class Workload:
         return 4000 + self.seed
 
 
-# The five workloads.  C1 is the small parity case; C2 is the plain FP32
-# 1M x 96 workload the benchmark times; C3-C5 are the precision, serving and
+# The workloads.  C1 is the small parity case; C2 is the plain FP32 1M x 96
+# workload the benchmark times; C3-C5 are the precision, serving and
 # memory-bounded shapes.
 WORKLOADS = {
     "c1_mixture_20k_d96": Workload("c1_mixture_20k_d96", "mixture", 20_000, 96, 200, 32, 32, 0.25, 32, 256,
@@ -64,9 +64,14 @@ WORKLOADS = {
     "c3_powerlaw_2m_d768": Workload("c3_powerlaw_2m_d768", "powerlaw", 2_000_000, 768, 10_000, 48, 48, 0.25, 128,
                                     4096, 10, (64, 128, 256), 1, power=1.0, unit_norm=True, seed=3,
                                     reduced_dtypes=("f32", "bf16", "fp8")),
+    # 10,000 well-separated components: 32,768 entries (about 3 per component)
+    # let fast entry selection land each query in its own component
     "c4_mixture_10m_d256": Workload("c4_mixture_10m_d256", "mixture", 10_000_000, 256, 10_000, 32, 32, 0.20, 64,
-                                    4096, 10, tuple(range(32, 513, 32)), 0, n_comp=10_000, sigma=0.3, seed=4,
+                                    32768, 10, tuple(range(32, 513, 32)), 0, n_comp=10_000, sigma=0.3, seed=4,
                                     reduced_dtypes=("bf16",)),
+    "c5_powerlaw_25m_d768": Workload("c5_powerlaw_25m_d768", "powerlaw", 25_000_000, 768, 10_000, 32, 32, 0.15,
+                                     128, 4096, 10, (64, 128, 192, 256, 384, 512), 1, power=1.0, unit_norm=True,
+                                     seed=5, reduced_dtypes=("bf16",), extra={"device_base": True}),
 }
 
 
@@ -128,3 +133,30 @@ def generate(w: Workload, n: int | None = None, nq: int | None = None, chunk: in
     else:
         raise ValueError(w.kind)
     return base, queries
+
+
+def generate_base_on_device(w: Workload, n: int | None = None, device="cuda", chunk: int = 1 << 20):
+    """A power-law base set drawn on the GPU, for workloads whose base set is
+    too large to hold twice in host memory (the 25M x 768 one: 77 GB).  Same
+    spectrum and the same rotation as ``generate`` (the rotation is the data
+    generator's first draw); the normal samples come from torch's generator
+    seeded with the data seed, so the rows differ from ``generate``'s but are
+    a pure function of the seed.  Returns an n x d float32 CUDA tensor."""
+    import torch
+    if w.kind != "powerlaw":
+        raise ValueError("generate_base_on_device draws power-law base sets")
+    n = w.n if n is None else n
+    rot = haar_rotation(w.d, np.random.default_rng(w.data_seed))
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(w.data_seed)
+    std = torch.arange(1, w.d + 1, dtype=torch.float64, device=dev).pow(-w.power / 2.0).float()
+    rot_t = torch.from_numpy(rot.T.astype(np.float32)).to(dev)
+    X = torch.empty((n, w.d), dtype=torch.float32, device=dev)
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        x = (torch.randn((m, w.d), generator=g, device=dev, dtype=torch.float32) * std) @ rot_t
+        if w.unit_norm:
+            x /= torch.linalg.vector_norm(x.double(), dim=1, keepdim=True).float()
+        X[s:s + m] = x
+    return X

@@ -112,3 +112,26 @@ def test_save_load_keeps_entry_clusters(tmp_path, c1_small):
     back = index_build.load_index(str(tmp_path))
     assert np.array_equal(back.entry_cluster, idx.entry_cluster)
     assert np.array_equal(back.cluster_centroids, idx.cluster_centroids)
+
+
+def test_ivf_candidates_are_exact_sorted_and_mostly_the_nearest():
+    """Inverted-list candidates (for base sets too large for the exact
+    search): every candidate's distance is its exact FP32 squared distance,
+    a row never lists itself, rows are in (distance, id) order, and on a
+    well-separated mixture most true nearest neighbours are found."""
+    rng = np.random.default_rng(4)
+    centres = rng.standard_normal((40, 16)) * 8.0
+    X = (centres[rng.integers(0, 40, 6000)] + 0.5 * rng.standard_normal((6000, 16))).astype(np.float32)
+    ids, dst = index_build.ivf_candidates(X, 12, nlist=24, nprobe=4, seed=3)
+    ids, dst = ids.numpy(), dst.numpy()
+    ex_ids, _ = index_build.knn_candidates(X, 12)
+    ex_ids = ex_ids.numpy()
+    for i in rng.integers(0, 6000, 200):
+        c = ids[i][ids[i] >= 0]
+        d = ((X[i].astype(np.float64) - X[c].astype(np.float64)) ** 2).sum(1)
+        np.testing.assert_allclose(dst[i][:len(c)], d, rtol=2e-6)
+        assert i not in c
+        key = list(zip(dst[i][:len(c)].tolist(), c.tolist()))
+        assert key == sorted(key)
+    recall = np.mean([len(set(a) & set(b)) / 12 for a, b in zip(ids, ex_ids)])
+    assert recall > 0.95, recall
