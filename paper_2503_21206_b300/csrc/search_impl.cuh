@@ -533,21 +533,33 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
     const int lo_pos = __reduce_min_sync(kFull, np);
     __syncwarp();
     if (lo_pos >= Snew) return;
-    for (int c = (Snew - 1) >> 5; c >= (lo_pos >> 5); --c) {
-        const int base = c << 5;
-        const int pos = base + lane;
-        const unsigned bit = (mine && np >= base && np < base + 32) ? (1u << (np - base)) : 0u;
-        const unsigned mask_c = __reduce_or_sync(kFull, bit);
-        const int before = __popc(__ballot_sync(kFull, mine && np < base));
-        const bool write = pos < Snew && pos >= lo_pos;
-        uint64_t val = 0;
-        if (write) {
-            const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-            const int kle = before + __popc(mask_c & upto);
-            val = ((mask_c >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos - kle];
+    // two 32-position chunks per step, from the last one down
+    const int c_lo = lo_pos >> 5;
+    const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+    for (int c = (Snew - 1) >> 5; c >= c_lo; c -= 2) {
+        const bool two = c - 1 >= c_lo;
+        const int base0 = c << 5, base1 = base0 - 32;
+        const unsigned bit0 = (mine && np >= base0 && np < base0 + 32) ? (1u << (np - base0)) : 0u;
+        const unsigned bit1 = (two && mine && np >= base1 && np < base0) ? (1u << (np - base1)) : 0u;
+        const unsigned m0 = __reduce_or_sync(kFull, bit0);
+        const unsigned m1 = __reduce_or_sync(kFull, bit1);
+        const int before0 = __popc(__ballot_sync(kFull, mine && np < base0));
+        const int before1 = before0 - __popc(m1);
+        const int pos0 = base0 + lane, pos1 = base1 + lane;
+        const bool wr0 = pos0 < Snew && pos0 >= lo_pos;
+        const bool wr1 = two && pos1 >= lo_pos;
+        uint64_t v0 = 0, v1 = 0;
+        if (wr0) {
+            const int kle = before0 + __popc(m0 & upto);
+            v0 = ((m0 >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos0 - kle];
+        }
+        if (wr1) {
+            const int kle = before1 + __popc(m1 & upto);
+            v1 = ((m1 >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos1 - kle];
         }
         __syncwarp();
-        if (write) A[pos] = val;
+        if (wr0) A[pos0] = v0;
+        if (wr1) A[pos1] = v1;
         __syncwarp();
     }
     w.S = Snew;

@@ -623,8 +623,10 @@ def exact_topk(X: np.ndarray, Q: np.ndarray, k: int, metric: int = 0, device=Non
     uncertified queries are recomputed over all rows in FP64."""
     dev = _dev(device)
     Xt = _as_tensor(X, dev)
-    xn = (Xt.double() ** 2).sum(1)
     n, d = X.shape
+    xn = torch.empty(n, dtype=torch.float64, device=dev)
+    for r in range(0, n, 1 << 20):   # FP64 norms in row chunks (a whole FP64 copy may not fit)
+        xn[r:r + (1 << 20)] = (Xt[r:r + (1 << 20)].double() ** 2).sum(1)
     kk = min(k + margin, n)
     ids_out = np.empty((Q.shape[0], k), np.int32)
     d_out = np.empty((Q.shape[0], k), np.float64)
