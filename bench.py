@@ -73,15 +73,19 @@ def aggregate_throughput(units_per_rank: int, world: int, max_seconds: float) ->
 
 # ----------------------------------------------------------------- inputs --
 
-def _cache_dir(name: str, n: int | None) -> str:
+def _cache_dir(name: str, n: int | None, nq_gen: int | None = None) -> str:
     base = os.environ.get("PILOT_BENCH_CACHE", os.path.join(tempfile.gettempdir(), "pilot_bench_cache"))
-    return os.path.join(base, f"{name}_n{n or 'full'}")
+    return os.path.join(base, f"{name}_n{n or 'full'}" + (f"_q{nq_gen}" if nq_gen else ""))
 
 
 def load_workload(name: str, n: int | None = None, nq: int | None = None, verbose: bool = True):
     """(workload, index data, queries, exact top-k ids), cached on disk.  The
-    query generator is prefix-stable, so ``nq`` takes the first nq queries."""
-    w, idx, Q, gt = _load_full(name, n, verbose)
+    query generator is prefix-stable, so ``nq`` takes the first nq queries;
+    an ``nq`` above the workload's own query count draws that many (the first
+    ones are the workload's queries)."""
+    from paper_2503_21206_b300 import synth
+    more = nq if nq is not None and nq > synth.WORKLOADS[name].nq else None
+    w, idx, Q, gt = _load_full(name, n, verbose, more)
     if nq is not None:
         Q, gt = Q[:nq], gt[:nq]
     return w, idx, np.ascontiguousarray(Q), gt
@@ -91,25 +95,25 @@ _BUILT = {}   # in-process cache of workloads too large for the disk cache
 DISK_CACHE_MAX_FLOATS = 500_000_000
 
 
-def _load_full(name: str, n: int | None, verbose: bool):
+def _load_full(name: str, n: int | None, verbose: bool, nq_gen: int | None = None):
     import torch
     from paper_2503_21206_b300 import index_build, synth
     w = synth.WORKLOADS[name]
-    if (name, n) in _BUILT:
-        return _BUILT[(name, n)]
-    cdir = _cache_dir(name, n)
+    if (name, n, nq_gen) in _BUILT:
+        return _BUILT[(name, n, nq_gen)]
+    cdir = _cache_dir(name, n, nq_gen)
     if os.path.exists(os.path.join(cdir, "done")):
         idx = index_build.load_index(cdir)
         return w, idx, np.load(os.path.join(cdir, "queries.npy")), np.load(os.path.join(cdir, "gt.npy"))
     dev = "cuda" if torch.cuda.is_available() else None
     t0 = time.time()
-    idx, Q, _, _ = index_build.build_workload(w, device=dev, n=n)
+    idx, Q, _, _ = index_build.build_workload(w, device=dev, n=n, nq=nq_gen)
     t1 = time.time()
     gt, _ = index_build.exact_topk(idx.full, Q, w.k, metric=w.metric, device=dev)
     if verbose:
         print(f"[bench] built {name}: index {t1 - t0:.1f}s, ground truth {time.time() - t1:.1f}s", file=sys.stderr)
     if idx.n * idx.d > DISK_CACHE_MAX_FLOATS:   # too large to write out: keep it for this process only
-        _BUILT[(name, n)] = (w, idx, Q, gt)
+        _BUILT[(name, n, nq_gen)] = (w, idx, Q, gt)
         return w, idx, Q, gt
     os.makedirs(cdir, exist_ok=True)
     index_build.save_index(idx, cdir)
@@ -555,11 +559,22 @@ def run_memory_bounded(args):
                       "mean_counters": {nm: round(float(c[:, i].mean()), 1) for i, nm in
                                         enumerate(["exp1", "dist1", "exp2", "dist2", "exp3", "dist3", "rerank"])}})
         print(json.dumps(batch[-1]), file=sys.stderr, flush=True)
+    # the same index with the full vectors in device memory, for comparison
+    g_dev = pilot.load_index_data(idx)
+    for b in batch:
+        step_ms, search_ms = timed_steps(lambda: pilot.pilot_search_ex(g_dev, qd, k, b["ef"], ids, dists, stream,
+                                                                       kernel_ms=kms),
+                                         stream, flush, args.steps, args.warmup, kms)
+        b["device_resident_qps"] = nq / (step_ms / 1000.0)
+    g_dev.free()
     at = {}
     for target in (0.9, 0.95):
         hit = next((b for b in batch if b["recall@10"] >= target), None)
         at[str(target)] = None if hit is None else {"ef": hit["ef"], "qps": round(hit["qps"], 1),
-                                                     "recall@10": hit["recall@10"]}
+                                                     "recall@10": hit["recall@10"],
+                                                     "device_resident_qps": round(hit["device_resident_qps"], 1)}
+    best = max(batch, key=lambda b: b["recall@10"])
+    at["max_recall"] = {"ef": best["ef"], "qps": round(best["qps"], 1), "recall@10": best["recall@10"]}
     ef_set = [e for e in (128, 256) if e in w.efs] or list(w.efs[:2])
     base_qps = min(b["qps"] for b in batch if b["ef"] in ef_set)
     rate = 0.6 * base_qps
@@ -694,6 +709,43 @@ def run_sweep_sub(args):
     print(json.dumps({"metric": "QPS@recall10=0.95 by sampling ratio x SVD ratio", "workload": args.workload,
                       "n": n, "d": d, "nq": nq, "plain_final_stage": base_plain, "cells": cells,
                       "data": "synthetic"}), flush=True)
+    return 0
+
+
+def run_gather_ceiling(args):
+    """Random-row read bandwidth of this GPU for the row sizes the search
+    kernel reads (32 B visited buckets, 128 B adjacency rows, full and
+    reduced rows): torch.embedding_bag sums bags of 64 random rows of a
+    4 GB table, so nearly all DRAM traffic is the random reads.  A ceiling
+    for the search kernel's access pattern beside the streaming copy peak;
+    the library's kernels play no part in it."""
+    import torch
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    table_bytes, gathered, bag = 4 << 30, 2 << 30, 64
+    out = []
+    for row_bytes in (32, 128, 384, 3072):
+        n_rows = table_bytes // row_bytes
+        table = torch.ones((n_rows, row_bytes // 4), dtype=torch.float32, device=device)
+        m = gathered // row_bytes // bag * bag
+        idx = torch.randint(0, n_rows, (m,), device=device, generator=torch.Generator(device).manual_seed(1))
+        offs = torch.arange(0, m, bag, device=device)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for rep in range(args.warmup + args.steps):
+            ev0.record()
+            torch.nn.functional.embedding_bag(idx, table, offs, mode="sum")
+            ev1.record()
+            ev1.synchronize()
+            if rep >= args.warmup:
+                ts.append(ev0.elapsed_time(ev1) / 1000.0)
+        t = statistics.median(ts)
+        out.append({"row_bytes": row_bytes, "rows": m, "random_read_gbs": round(m * row_bytes / t / 1e9, 1),
+                    "ms": round(t * 1000, 3)})
+        del table, idx, offs
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "random-row read bandwidth", "unit": "GB/s", "method": "torch embedding_bag, "
+                      f"sum over bags of {bag} random rows of a 4 GB table", "rows": out}), flush=True)
     return 0
 
 
@@ -999,7 +1051,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="c2_aniso_1m_d96")
     ap.add_argument("--ef", type=int, default=0, help="a fixed ef instead of the recall-0.95 sweep")
     ap.add_argument("--n", type=int, default=None, help="smaller base set (profiling cases)")
-    ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling cases)")
+    ap.add_argument("--nq", type=int, default=None, help="queries: fewer takes a prefix, more draws them from the same generator (profiling cases)")
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--stage-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1026,6 +1078,8 @@ def main(argv=None):
     ap.add_argument("--memory-bounded", action="store_true",
                     help="the memory-bounded configuration (full vectors in pinned host memory): QPS at recall "
                          "0.9 / 0.95 and a mixed-ef serving run; e.g. --workload c5_powerlaw_25m_d768 --nq 2000")
+    ap.add_argument("--gather-ceiling", action="store_true",
+                    help="random-row read bandwidth for the row sizes the search reads (context for the roofline)")
     ap.add_argument("--forms", action="store_true",
                     help="compare the reduced-row precision forms and the plain form (one GPU)")
     args = ap.parse_args(argv)
@@ -1039,6 +1093,8 @@ def main(argv=None):
         return run_serve_sweep(args)
     if args.memory_bounded:
         return run_memory_bounded(args)
+    if args.gather_ceiling:
+        return run_gather_ceiling(args)
     if args.tau:
         return run_tau(args)
     if args.sweep_sub:

@@ -95,7 +95,7 @@ def knn_candidates(X: np.ndarray, k: int, device=None, chunk: int = 4096, exclud
     dev = _dev(device)
     Xt = _as_tensor(X, dev)
     n = Xt.shape[0]
-    norms = (Xt.double() ** 2).sum(1).float()
+    norms = torch.cat([(Xt[r:r + (1 << 20)].double() ** 2).sum(1) for r in range(0, n, 1 << 20)]).float()
     k_eff = min(k, n - 1 if exclude_self else n)
     ids = torch.empty((n, k_eff), dtype=torch.int64, device=dev)
     dst = torch.empty((n, k_eff), dtype=torch.float32, device=dev)
