@@ -122,14 +122,16 @@ typedef struct {
 /*
  * Copy an index to the current CUDA device.  *out receives the handle.  Besides
  * the arrays, the index holds the searches' visited sets: one hash table per
- * resident search warp (16 per SM) of 4 x pow2(1.25 x PILOT_MAX_EF x max(R,
- * R_sub)) bytes, e.g. 128 KB per warp and 310 MB in all at degree 32 on a
- * 148-SM GPU, whatever n is.  A search with list size ef uses pow2(1.25 x
- * max(ef, 32) x max(R, R_sub)) entries of it (at least 4096).  Each set carries an epoch tag, so a
- * new one costs nothing until the tag's epochs run out (2^(32 - bits of n-1)
- * - 1 of them) and the table is cleared; the environment variable
- * PILOT_VISITED_EPOCH_CYCLE=<c>, read here, shortens that cycle to c sets (a
- * testing aid: it only clears more often).
+ * resident search warp (16 per SM) of 2 x pow2(1.25 x PILOT_MAX_EF x max(R,
+ * R_sub)) bytes (16-bit words, 15 entries per 16), e.g. 64 KB per warp and
+ * 155 MB in all at degree 32 on a 148-SM GPU, whatever n is below 2^24 (from
+ * there on each table takes at least 2^(bits of n-1 - 8) bytes).  A search
+ * with list size ef uses pow2(1.25 x max(ef, 32) x max(R, R_sub)) words of it
+ * (at least 4096).  Each set carries a 12-bit epoch tag in the bucket headers,
+ * so a new one costs nothing until the epochs run out (4095 sets) and the
+ * table is cleared; the environment variable PILOT_VISITED_EPOCH_CYCLE=<c>,
+ * read here, shortens that cycle to c sets (a testing aid: it only clears
+ * more often).
  */
 pilot_status pilot_index_load(const pilot_index_desc* desc, pilot_index** out);
 
@@ -198,9 +200,10 @@ typedef struct {
                                    < n and distinct within a row (PILOT_EINVAL otherwise).
                                    Counters: [6] = seeds scored, [7] = -1 */
     int32_t seed_count;         /* entries per row of seed_ids, 1..ef */
-    int32_t visited_entries;    /* entries of the visited table this call uses per warp: 0 =
-                                   automatic (pow2(1.25 x max(ef, 32) x max(R, R_sub)), at least
-                                   4096), else a cap, a power of two from 256 to the index's table
+    int32_t visited_entries;    /* 16-bit words of the visited table this call uses per warp:
+                                   0 = automatic (pow2(1.25 x max(ef, 32) x max(R, R_sub)), at
+                                   least 4096), else a cap, a power of two from
+                                   max(256, 2^(bits of n-1 - 9)) to the index's table
                                    (PILOT_EINVAL otherwise).  A smaller table trades L2 reuse for
                                    insertions that find no room (status word [7]); results do
                                    not change */

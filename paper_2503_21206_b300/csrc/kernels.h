@@ -41,47 +41,66 @@ struct DevIndex {
     const int32_t* cl_entries;
     const int32_t* cl_offsets;   // n_clusters + 1
     // Visited sets: one open-addressing hash table per warp slot (vis_slots
-    // slots, vis_stride 32-bit entries each, a power of two), in buckets of 8
-    // entries (one 32-byte sector).  An entry holds (epoch << id_bits) | id;
-    // entries of another epoch are free, so a new set costs one epoch step and
-    // a slot is cleared only when its epoch counter wraps.  The size depends
-    // on ef and the degree, not on n.  vis_epoch holds each slot's running
-    // epoch counter across launches.
-    uint32_t* vis;
+    // slots of vis_stride 16-bit words each, a power of two), in 32-byte
+    // buckets of 16 words (one sector): word 0 is the bucket's header
+    // (epoch << 4 | count), words 1..15 its entries.  A node is split by a
+    // bijection of [0, 2^id_bits) into a bucket index and a quotient, so an
+    // entry stores only the quotient and its distance from the home bucket
+    // (see visit() in search_impl.cuh); a bucket whose header carries another
+    // epoch is empty, so a new set costs one epoch step and a slot is cleared
+    // only when its epoch counter wraps.  The size depends on ef and the
+    // degree, not on n (beyond a floor of 2^(id_bits - 9) words that keeps
+    // quotients within 13 bits).  vis_epoch holds each slot's running epoch
+    // counter across launches.
+    uint16_t* vis;
     uint32_t* vis_epoch;
     int64_t vis_stride;
     int vis_slots;
     int id_bits;         // bits of a node id: n - 1 < 2^id_bits
-    uint32_t epoch_max;  // epochs per cycle: at most 2^(32 - id_bits) - 1
+    uint32_t epoch_max;  // epochs per cycle: at most kVisEpochs
 };
 
-constexpr int kVisBucket = 8;      // entries per bucket (32 bytes)
-constexpr int kVisMaxProbe = 32;   // buckets probed before an insertion gives up
+constexpr int kVisBucket = 16;       // 16-bit words per bucket (32 bytes): a header and 15 entries
+constexpr int kVisMaxProbe = 7;      // buckets probed (home + 0..6) before an insertion gives up
+constexpr uint32_t kVisEpochs = 4095;  // 12-bit epoch field of a bucket header
+constexpr int kVisQuotientBits = 13;   // an entry is (quotient << 3) | (probe + 1)
 
-// Entries of the visited table a search with list size ef uses: the power of
-// two >= 1.25 x max(ef, 32) x the larger degree, at least 4096.  A set (stage
-// (1), or the re-rank with stages (2) and (3)) visits at most (its expansions
-// + 1) x degree nodes; measured, under 0.8 x ef x degree plus ef at ef >= 64,
-// so the table stays at most about 60% full.
-__host__ __device__ inline int64_t vis_entries_for(int ef, int max_degree) {
+// Words of the visited table a search with list size ef uses: the power of
+// two >= 1.25 x max(ef, 32) x the larger degree, at least 4096 and at least
+// 2^(id_bits - 9) (so that 2^(id_bits - 13) buckets or more leave quotients of
+// at most 13 bits).  A set (stage (1), or the re-rank with stages (2) and
+// (3)) visits at most (its expansions + 1) x degree nodes; measured, under
+// 0.8 x ef x degree plus ef at ef >= 64, so the 15 entries of each 16 words
+// stay at most about 70% full.
+__host__ __device__ inline int64_t vis_entries_for(int ef, int max_degree, int id_bits) {
     int64_t want = int64_t(ef < 32 ? 32 : ef) * max_degree * 5 / 4, h = 4096;
+    const int64_t floor_words = id_bits > 9 ? (int64_t(1) << (id_bits - 9)) : 1;
+    if (want < floor_words) want = floor_words;
     while (h < want) h <<= 1;
     return h;
 }
 
-// Bucket mask and hash shift of a table of vis_entries_for(ef, max_degree)
-// entries, capped at entries_per_slot (both powers of two >= 256).
+// Smallest table (in words) a search may be capped to on an index with
+// id_bits-bit ids: 256, or the quotient floor when larger.
+__host__ __device__ inline int64_t vis_min_entries(int id_bits) {
+    const int64_t f = id_bits > 9 ? (int64_t(1) << (id_bits - 9)) : 1;
+    return f > 256 ? f : 256;
+}
+
+// Bucket mask and quotient width of a table of vis_entries_for(ef, ...)
+// words, capped at entries_per_slot (both powers of two >= vis_min_entries).
 struct VisSize {
     uint32_t mask;
-    int shift;
+    int qbits;
 };
-__host__ __device__ inline VisSize vis_size_for(int ef, int max_degree, int64_t entries_per_slot) {
-    int64_t h = vis_entries_for(ef, max_degree);
+__host__ __device__ inline VisSize vis_size_for(int ef, int max_degree, int id_bits, int64_t entries_per_slot) {
+    int64_t h = vis_entries_for(ef, max_degree, id_bits);
     if (h > entries_per_slot) h = entries_per_slot;
     const int64_t buckets = h / kVisBucket;
     int lg = 0;
     while ((int64_t(1) << lg) < buckets) ++lg;
-    return VisSize{uint32_t(buckets - 1), 32 - lg};
+    const int q = id_bits - lg;
+    return VisSize{uint32_t(buckets - 1), q > 0 ? q : 0};
 }
 
 struct SearchConfig {
@@ -92,7 +111,7 @@ struct SearchConfig {
     int fes_seeds;       // entries seeding stage (1) (1..kFesT)
     int stage_bytes;     // per-warp row staging buffer
     uint32_t vis_mask;   // buckets of the visited table in use - 1 (a power of two - 1)
-    int vis_shift;       // 32 - log2(buckets): the hash keeps the top bits
+    int vis_qbits;       // quotient bits of a visited entry: id_bits - log2(buckets), at most 13
     int filter;          // 1: certified FP32 pre-filter once the list is full
 };
 
@@ -151,7 +170,7 @@ struct ServeIO {
     const float* new_qp;
     const int32_t* new_fes_pos;
     const double* new_fes_lb;
-    uint32_t* vis;               // per slot, vis_stride entries of the index's layout
+    uint16_t* vis;               // per slot, vis_stride words of the index's layout
     int32_t* vis_overflow;       // device counter of visited insertions that found no room
     int32_t* res_ids;            // per slot, k_max (host-mapped)
     float* res_dists;            // per slot, k_max (host-mapped)

@@ -427,25 +427,26 @@ pilot_status pilot_index_load(const pilot_index_desc* dsc, pilot_index** out) {
     X.full = static_cast<const float*>(p);
     // visited sets: one hash table per warp slot the search kernel can keep
     // resident (16 per SM), each sized for the largest ef and the larger
-    // degree -- independent of n (at most 128 KB per slot)
+    // degree -- independent of n above a small floor (64 KB per slot at
+    // degree 32)
     {
         X.id_bits = 1;
         while ((int64_t(1) << X.id_bits) < n) ++X.id_bits;   // n - 1 < 2^id_bits <= 2^31
-        X.epoch_max = 0xFFFFFFFFu >> X.id_bits;
+        X.epoch_max = kVisEpochs;
         // a shorter epoch cycle (more frequent table clears) for tests of the wrap
         if (const char* ev = std::getenv("PILOT_VISITED_EPOCH_CYCLE")) {
             const long long c = std::atoll(ev);
             if (c >= 1 && uint64_t(c) < X.epoch_max) X.epoch_max = uint32_t(c);
         }
-        X.vis_stride = vis_entries_for(PILOT_MAX_EF, std::max(X.R, X.R_sub));
+        X.vis_stride = vis_entries_for(PILOT_MAX_EF, std::max(X.R, X.R_sub), X.id_bits);
         const int64_t slots = int64_t(ix->num_sms) * 16;
         X.vis_slots = int(slots);
-        const size_t bytes = size_t(slots) * size_t(X.vis_stride) * 4;
+        const size_t bytes = size_t(slots) * size_t(X.vis_stride) * sizeof(uint16_t);
         void* p1 = nullptr;
         CUDA_TRY(cudaMalloc(&p1, bytes));
         ix->allocs.push_back(p1);
         CUDA_TRY(cudaMemset(p1, 0, bytes));
-        X.vis = static_cast<uint32_t*>(p1);
+        X.vis = static_cast<uint16_t*>(p1);
         void* p2 = nullptr;
         CUDA_TRY(cudaMalloc(&p2, size_t(slots) * 4));
         ix->allocs.push_back(p2);
@@ -616,9 +617,10 @@ pilot_status pilot_search_ex(pilot_index* ix, const float* queries, int64_t nq, 
     if (rows > 0) set_stage_rows(X, cfg, rows);
     if (opt.visited_entries != 0) {
         const int64_t v = opt.visited_entries;
-        if (v < 256 || v > X.vis_stride || (v & (v - 1)))
-            return fail(PILOT_EINVAL, "visited_entries = %lld must be 0 or a power of two in [256, %lld]",
-                        (long long)v, (long long)X.vis_stride);
+        const int64_t vmin = vis_min_entries(X.id_bits);
+        if (v < vmin || v > X.vis_stride || (v & (v - 1)))
+            return fail(PILOT_EINVAL, "visited_entries = %lld must be 0 or a power of two in [%lld, %lld]",
+                        (long long)v, (long long)vmin, (long long)X.vis_stride);
         set_visited_size(X, cfg, v);
     }
 

@@ -57,9 +57,9 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
 }
 
 void set_visited_size(const DevIndex& ix, SearchConfig& cfg, int64_t entries_per_slot) {
-    const VisSize v = vis_size_for(cfg.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, entries_per_slot);
+    const VisSize v = vis_size_for(cfg.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.id_bits, entries_per_slot);
     cfg.vis_mask = v.mask;
-    cfg.vis_shift = v.shift;
+    cfg.vis_qbits = v.qbits;
 }
 
 void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {

@@ -79,9 +79,9 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
 
 struct Warp {
     uint64_t* pool;
-    uint32_t* vis;       // this warp slot's visited table
+    uint16_t* vis;       // this warp slot's visited table
     uint32_t vis_mask;   // buckets in use - 1
-    int vis_shift;       // 32 - log2(buckets)
+    int vis_qbits;       // quotient bits of an entry
     int id_bits;
     int overflow;        // insertions that found no room (visited again if met again)
     int32_t* cand;
@@ -95,9 +95,10 @@ struct Warp {
     int ef;         // this query's list size
     int lb;         // every candidate before position lb is checked
     uint32_t epoch_ctr;
-    uint32_t epoch;  // 1..255: the current stage's visited tag
+    uint32_t epoch;  // 1..kVisEpochs: the current set's bucket-header tag
     int lane;
     uint64_t* bar;      // mbarrier of this warp's row gathers
+    const uint8_t* red_base;   // the reduced rows (kept in L2 by a cache policy)
     uint32_t phase;     // parity of the barrier phase being waited for
     bool failed;        // a gather did not complete within kMaxPolls polls
 #ifdef PILOT_CHECKED
@@ -106,48 +107,79 @@ struct Warp {
 };
 
 // ------------------------------------------------------------ visited set --
-// Bucket of node v: the top bits of a multiplicative hash (Knuth's constant).
-__device__ __forceinline__ uint32_t vis_bucket(const Warp& w, int32_t v) {
-    return (uint32_t(v) * 0x9E3779B1u) >> w.vis_shift;
+// Node v is mapped by h, a bijection of [0, 2^id_bits) (multiply by an odd
+// constant, xor-shift, multiply: each step is invertible on id_bits bits), to
+// its home bucket, the top bits of h, and its quotient s, the low vis_qbits
+// bits.  The pair (bucket, s) identifies v, so an entry holds only s and the
+// probe r at which v was placed, home + r: (s << 3) | (r + 1), never zero.
+// Bucket layout (16 words, one 32-byte sector): word 0 = epoch << 4 | count,
+// words 1..count the entries.  A bucket is zeroed when it is first written in
+// an epoch, so the words past its count are zero and a lookup may compare
+// all 15 without masking.
+__device__ __forceinline__ uint32_t vis_hash(uint32_t v, int bits) {
+    const uint32_t m = bits >= 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+    uint32_t h = (v * 0x9E3779B1u) & m;
+    h ^= h >> ((bits + 1) >> 1);
+    return (h * 0x85EBCA77u) & m;
 }
 
+// Nonzero when some 16-bit half of x is zero (a borrow out of a zero low half
+// can only flag the high half as well, so the test is exact as an "any").
+__device__ __forceinline__ uint32_t zero_half(uint32_t x) { return (x - 0x00010001u) & ~x & 0x80008000u; }
+
 // Probe-and-insert of node v for every lane with `valid`: returns true when v
-// is not yet in the current set, and records it.  Lanes probe their bucket
-// (8 entries, one 32-byte sector) in parallel; lanes that need room in the
-// same bucket take its free entries in lane order, and those left without
-// one move on to the next bucket (linear probing over buckets).  Entries are
-// never removed within a set, so a bucket with a free entry ends the search
-// for v.  The valid lanes' ids must be distinct.  An insertion that finds no
-// room within kVisMaxProbe buckets reports v as new without recording it; if
-// v is met again it is scored again, and the merge drops its equal key, so
-// results are unchanged (only the distance counter grows).
+// is not yet in the current set, and records it.  Lanes probe their bucket in
+// parallel; lanes that need room in the same bucket take its free entries in
+// lane order (the first of them also writes the header, zeroing a bucket of
+// an older epoch first), and those left without one move on to the next
+// bucket (linear probing).  Counts only grow within a set, so a bucket with
+// room ends the search for v.  The valid lanes' ids must be distinct.  An
+// insertion that finds no room within kVisMaxProbe buckets reports v as new
+// without recording it; if v is met again it is scored again, and the merge
+// drops its equal key, so results are unchanged (only the distance counter
+// grows).
 __device__ __forceinline__ bool visit(Warp& w, int32_t v, bool valid) {
-    const uint32_t tag = (w.epoch << w.id_bits) | uint32_t(v);
-    uint32_t b = valid ? vis_bucket(w, v) : 0u;
+    const uint32_t h = valid ? vis_hash(uint32_t(v), w.id_bits) : 0u;
+    uint32_t b = h >> w.vis_qbits;
+    const uint32_t s3 = (h & ((1u << w.vis_qbits) - 1u)) << 3;
     bool pending = valid, isnew = false;
 #pragma unroll 1
-    for (int probe = 0; probe < kVisMaxProbe; ++probe) {
+    for (int r = 0; r < kVisMaxProbe; ++r) {
         if (!__any_sync(kFull, pending)) break;
-        unsigned freem = 0;
+        uint16_t* bp = w.vis + size_t(b) * kVisBucket;
+        int cnt = 0;
+        bool stale = false;
         if (pending) {
-            const uint4* bp = reinterpret_cast<const uint4*>(w.vis + size_t(b) * kVisBucket);
-            const uint4 x = bp[0], y = bp[1];
-            const uint32_t e[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-            bool found = false;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                found |= e[i] == tag;
-                freem |= unsigned((e[i] >> w.id_bits) != w.epoch) << i;
+            const uint4 x = *reinterpret_cast<const uint4*>(bp), y = *reinterpret_cast<const uint4*>(bp + 8);
+            stale = ((x.x & 0xFFFFu) >> 4) != w.epoch;
+            if (!stale) {
+                cnt = int(x.x & 15u);
+                const uint32_t t2 = (s3 | uint32_t(r + 1)) * 0x10001u;
+                // word 0's low half is the header: forced nonzero, never a match
+                const uint32_t z = zero_half((x.x ^ t2) | 0x8000u) | zero_half(x.y ^ t2) | zero_half(x.z ^ t2) |
+                                   zero_half(x.w ^ t2) | zero_half(y.x ^ t2) | zero_half(y.y ^ t2) |
+                                   zero_half(y.z ^ t2) | zero_half(y.w ^ t2);
+                if (z) pending = false;
             }
-            if (found) pending = false;
         }
         const unsigned peers = __match_any_sync(kFull, pending ? b : (0x80000000u | unsigned(w.lane)));
+        const int rank = __popc(peers & lanemask_lt());
+        const int room = (kVisBucket - 1) - cnt;
+        if (pending && rank == 0 && room > 0) {
+            const int np = __popc(peers);
+            const uint32_t hdr = (w.epoch << 4) | uint32_t(cnt + (np < room ? np : room));
+            if (stale) {
+                uint4* q = reinterpret_cast<uint4*>(bp);
+                q[0] = make_uint4(hdr, 0u, 0u, 0u);
+                q[1] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                bp[0] = uint16_t(hdr);
+            }
+        }
+        __syncwarp();
         if (pending) {
-            const int rank = __popc(peers & lanemask_lt());
-            if (rank < __popc(freem)) {
-                unsigned f = freem;   // the rank-th free entry (rank is almost always 0)
-                for (int r = 0; r < rank; ++r) f &= f - 1;
-                w.vis[size_t(b) * kVisBucket + (__ffs(f) - 1)] = tag;
+            if (rank < room) {
+                bp[1 + cnt + rank] = uint16_t(s3 | uint32_t(r + 1));
                 pending = false;
                 isnew = true;
             } else {
@@ -250,10 +282,11 @@ __device__ __forceinline__ void exact_chunk(DF& acc, uint4 v, const float* qc, f
 constexpr float kTiny = 1e-36f;
 
 // Plain FP32 accumulation of one 16-byte chunk of a row into two partial
-// sums a0, a1 (alternate elements, for instruction-level parallelism) and,
-// for the inner product, the sum of |q| |x| into b.
+// sums a.x, a.y (alternate elements, one packed FP32x2 operation per pair;
+// each half rounds exactly like its scalar counterpart) and, for the inner
+// product, the sum of |q| |x| into b.
 template <int DT, int METRIC>
-__device__ __forceinline__ void approx_chunk(float& a0, float& a1, float& b, uint4 v, const float* qc) {
+__device__ __forceinline__ void approx_chunk(float2& a, float& b, uint4 v, const float* qc) {
     const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
     float x[16], qa[16];
     constexpr int E = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
@@ -283,15 +316,15 @@ __device__ __forceinline__ void approx_chunk(float& a0, float& a1, float& b, uin
             x[h * 4 + 0] = c[0]; x[h * 4 + 1] = c[1]; x[h * 4 + 2] = c[2]; x[h * 4 + 3] = c[3];
         }
     }
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
     for (int e = 0; e < E; e += 2) {
+        const float2 qq = make_float2(qa[e], qa[e + 1]), xx = make_float2(x[e], x[e + 1]);
         if (METRIC == 0) {
-            const float t0 = __fsub_rn(qa[e], x[e]), t1 = __fsub_rn(qa[e + 1], x[e + 1]);
-            a0 = __fmaf_rn(t0, t0, a0);
-            a1 = __fmaf_rn(t1, t1, a1);
+            const float2 t = __ffma2_rn(xx, neg1, qq);   // fl(q - x) per half: -x is exact
+            a = __ffma2_rn(t, t, a);
         } else {
-            a0 = __fmaf_rn(qa[e], x[e], a0);
-            a1 = __fmaf_rn(qa[e + 1], x[e + 1], a1);
+            a = __ffma2_rn(qq, xx, a);
             b = __fmaf_rn(fabsf(qa[e]), fabsf(x[e]), b);
             b = __fmaf_rn(fabsf(qa[e + 1]), fabsf(x[e + 1]), b);
         }
@@ -313,11 +346,12 @@ __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float*
     const int row = rows(i);   // the staged row lane i tests
     const uint8_t* rowp = w.stage + row * stage_stride(row_bytes);
     const int nch = row_bytes >> 4;
-    float a0 = 0.0f, a1 = 0.0f, b = 0.0f;
+    float2 a = make_float2(0.0f, 0.0f);
+    float b = 0.0f;
 #pragma unroll 2
     for (int c = 0; c < nch; ++c)
-        approx_chunk<DT, METRIC>(a0, a1, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC);
-    const float A = __fadd_rn(a0, a1);
+        approx_chunk<DT, METRIC>(a, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC);
+    const float A = __fadd_rn(a.x, a.y);
     const float rel = float(n_elems + 8) * 1.1920928955078125e-7f;   // 2 (n + 8) u, u = 2^-24
     float lb;
     if (METRIC == 0) {
@@ -414,9 +448,12 @@ __device__ __forceinline__ void gather_issue(Warp& w, const uint8_t* __restrict_
     __syncwarp();
     if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
     __syncwarp();
-    if (w.lane < n)
-        bulk_copy_g2s(w.stage + w.lane * stage_stride(row_bytes), base + int64_t(w.cand[r0 + w.lane]) * row_bytes,
-                      uint32_t(row_bytes), w.bar);
+    if (w.lane < n) {
+        // reduced rows (small, reused across queries) stay in L2; full rows stream
+        const uint64_t pol = base == w.red_base ? l2_evict_last_policy() : l2_evict_first_policy();
+        bulk_copy_g2s_hint(w.stage + w.lane * stage_stride(row_bytes),
+                           base + int64_t(w.cand[r0 + w.lane]) * row_bytes, uint32_t(row_bytes), w.bar, pol);
+    }
 }
 
 __device__ __forceinline__ void gather_wait(Warp& w) {
@@ -465,8 +502,11 @@ template <int DT, int METRIC>
 __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict__ base, int row_bytes,
                                               const float* __restrict__ scales, const float* q, int m,
                                               int stage_bytes, bool plain, bool filter, float thr, int n_elems) {
-    int P = stage_bytes / stage_stride(row_bytes);
-    P = P >= kCand ? kCand : (P & ~3);
+    int P = m;   // one pass when the staging buffer holds every row (no division on this path)
+    if (m * stage_stride(row_bytes) > stage_bytes) {
+        P = stage_bytes / stage_stride(row_bytes);
+        P = P >= kCand ? kCand : (P & ~3);
+    }
     for (int r0 = 0; r0 < m; r0 += P) {
         const int r1 = r0 + P < m ? r0 + P : m;
         const int nr = r1 - r0;
@@ -533,6 +573,25 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
     const int lo_pos = __reduce_min_sync(kFull, np);
     __syncwarp();
     if (lo_pos >= Snew) return;
+    if (nb2 == 1) {
+        // one new key (the common case once C is full): shift C[lo_pos ..
+        // Snew - 2] up by one position, chunk by chunk from the last; each
+        // chunk's sources lie in the chunk itself or the one below, which is
+        // written only in the next iteration, after the barrier
+        for (int c = (Snew - 1) >> 5; c >= (lo_pos >> 5); --c) {
+            const int i = (c << 5) + lane;
+            const bool mv = i > lo_pos && i < Snew;
+            const uint64_t v = mv ? A[i - 1] : 0ull;
+            __syncwarp();
+            if (mv) A[i] = v;
+        }
+        __syncwarp();
+        if (mine) A[lo_pos] = key;
+        __syncwarp();
+        w.S = Snew;
+        if (lo_pos < w.lb) w.lb = lo_pos;
+        return;
+    }
     // two 32-position chunks per step, from the last one down
     const int c_lo = lo_pos >> 5;
     const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
@@ -612,15 +671,15 @@ struct QState {
 };
 
 // Start a new visited set for this warp slot.  Epochs cycle through 1..M,
-// M = epoch_max <= 2^(32 - id_bits) - 1 (the tag's epoch field); before a
-// cycle restarts the slot's whole table (stride entries) is cleared.
+// M = epoch_max <= kVisEpochs (the bucket header's epoch field); before a
+// cycle restarts the slot's whole table (stride words) is cleared.
 __device__ __forceinline__ void new_visited_set(Warp& w, int64_t stride, uint32_t M) {
     w.epoch_ctr += 1;
     const uint32_t r = M > 1 ? w.epoch_ctr % M : 0u;
     if (r == 0) {
         uint4* p = reinterpret_cast<uint4*>(w.vis);
-        const int64_t n4 = stride >> 2;
-        for (int64_t i = w.lane; i < n4; i += 32) p[i] = make_uint4(0u, 0u, 0u, 0u);
+        const int64_t n16 = stride >> 3;
+        for (int64_t i = w.lane; i < n16; i += 32) p[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     w.epoch = r + 1;
     __syncwarp();
@@ -704,7 +763,7 @@ struct Searcher {
         __syncwarp();
         for (int b0 = 0; b0 < W; b0 += 32) {
             const int j = b0 + lane;
-            int32_t v = j < W ? __ldg(row + j) : -1;
+            int32_t v = j < W ? ld_nc_hint(row + j, view == 3 ? l2_evict_first_policy() : l2_evict_last_policy()) : -1;
             PILOT_CHECK_INDEX(w, v, view == 3 ? ix.n : ix.n_sub);
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
             PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
@@ -1005,6 +1064,7 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
     w.stage = base + L.off_stage;
     w.phase = 0;
+    w.red_base = reinterpret_cast<const uint8_t*>(ix.red);
     w.failed = false;
     w.lane = threadIdx.x & 31;
     w.S = 0;
@@ -1014,7 +1074,7 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     w.epoch_ctr = 0;
     w.vis = nullptr;
     w.vis_mask = cfg.vis_mask;
-    w.vis_shift = cfg.vis_shift;
+    w.vis_qbits = cfg.vis_qbits;
     w.id_bits = ix.id_bits;
     w.overflow = 0;
     if (w.lane == 0) mbar_init(w.bar, 1);
@@ -1096,9 +1156,9 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
             w.epoch_ctr = ss->epoch_ctr;
             w.ef = e.ef;
             k = e.k;
-            const VisSize vs = vis_size_for(e.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.vis_stride);
+            const VisSize vs = vis_size_for(e.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.id_bits, ix.vis_stride);
             w.vis_mask = vs.mask;
-            w.vis_shift = vs.shift;
+            w.vis_qbits = vs.qbits;
             s.fes(st, sio.new_fes_pos + int64_t(e.new_idx) * cfg.fes_T, sio.new_fes_lb[e.new_idx]);
         } else {
             // a request that finished in the previous step is listed again
@@ -1114,9 +1174,9 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
             w.epoch_ctr = ss->epoch_ctr;
             w.epoch = ss->epoch;
             k = ss->k;
-            const VisSize vs = vis_size_for(w.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.vis_stride);
+            const VisSize vs = vis_size_for(w.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.id_bits, ix.vis_stride);
             w.vis_mask = vs.mask;
-            w.vis_shift = vs.shift;
+            w.vis_qbits = vs.qbits;
             for (int j = w.lane; j < w.S; j += 32) w.pool[j] = gpool[j];
             __syncwarp();
         }

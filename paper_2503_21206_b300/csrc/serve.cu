@@ -112,7 +112,7 @@ struct pilot_server {
     SlotState* state = nullptr;
     uint64_t* pool = nullptr;
     float *q_pad = nullptr, *qp = nullptr;
-    uint32_t* vis = nullptr;          // per slot, vis_stride entries (sized by max_ef and the degree)
+    uint16_t* vis = nullptr;          // per slot, vis_stride words (sized by max_ef and the degree)
     int64_t vis_stride = 0;
     int32_t* vis_overflow = nullptr;  // device counter
     int32_t *res_ids = nullptr, *res_done = nullptr, *res_counters = nullptr;   // host-mapped
@@ -388,9 +388,9 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     // HBM budget: per slot its list, query rows, state and visited table
     // (sized by max_ef and the degree, independent of n)
     const int pool_stride = [&] { int p = 32; while (p < c.max_ef) p <<= 1; return p; }();
-    S->vis_stride = vis_entries_for(int(c.max_ef), std::max(X.R, X.R_sub));
+    S->vis_stride = vis_entries_for(int(c.max_ef), std::max(X.R, X.R_sub), X.id_bits);
     const size_t per_slot = size_t(pool_stride) * 8 + size_t(X.d_pad + X.qp_pad) * 4 + sizeof(SlotState) +
-                            size_t(S->vis_stride) * 4;
+                            size_t(S->vis_stride) * sizeof(uint16_t);
     size_t free_b = 0, total_b = 0;
     if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return cuda_err(e, "cudaMemGetInfo");
     const size_t budget = c.hbm_budget_bytes > 0 ? size_t(c.hbm_budget_bytes) : free_b / 4;
@@ -416,7 +416,7 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
     if ((ps = S->dalloc(&S->vis, size_t(NS) * size_t(S->vis_stride))) != PILOT_OK) return ps;
     if ((ps = S->dalloc(&S->vis_overflow, 1)) != PILOT_OK) return ps;
     if ((e = cudaMemset(S->state, 0, size_t(NS) * sizeof(SlotState))) != cudaSuccess) return cuda_err(e, "clear");
-    if ((e = cudaMemset(S->vis, 0, size_t(NS) * size_t(S->vis_stride) * 4)) != cudaSuccess)
+    if ((e = cudaMemset(S->vis, 0, size_t(NS) * size_t(S->vis_stride) * sizeof(uint16_t))) != cudaSuccess)
         return cuda_err(e, "clear");
     if ((e = cudaMemset(S->vis_overflow, 0, 4)) != cudaSuccess) return cuda_err(e, "clear");
     if ((ps = S->halloc(&S->res_ids, size_t(NS) * c.max_k)) != PILOT_OK) return ps;
