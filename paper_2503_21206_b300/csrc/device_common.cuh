@@ -84,6 +84,49 @@ __device__ __forceinline__ void ip_acc2(DF& acc, float q, float xh, float xl) {
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, pe));
 }
 
+// The same transformations on two independent sums at once, with packed
+// FP32x2 operations (each half rounds exactly like the scalar operation);
+// a - b is written as fma(b, -1, a), one rounding.
+struct DF2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2& e) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bv = sub2(s, a);
+    const float2 av = sub2(s, bv);
+    e = __fadd2_rn(sub2(a, av), sub2(b, bv));
+    return s;
+}
+
+// acc += (q - x)^2 per half, as l2_acc: q - x = d + e exactly (TwoSum with
+// b = -x), d * d = p + pe exactly (with -pe = p - d * (-d) from one FMA, since
+// -d = x - q exactly), e^2 dropped.
+__device__ __forceinline__ void l2_acc_x2(DF2& acc, float2 q, float2 x) {
+    const float2 d = sub2(q, x);
+    const float2 bv = sub2(d, q);
+    const float2 av = sub2(d, bv);
+    const float2 e = sub2(sub2(q, av), __fadd2_rn(x, bv));
+    const float2 p = __fmul2_rn(d, d);
+    const float2 npe = __ffma2_rn(d, sub2(x, q), p);
+    float2 t;
+    acc.hi = two_sum2(acc.hi, p, t);
+    acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(t, sub2(__fmul2_rn(__fadd2_rn(d, d), e), npe)));
+}
+
+// acc += q * x per half, as ip_acc.
+__device__ __forceinline__ void ip_acc_x2(DF2& acc, float2 q, float2 x) {
+    const float2 p = __fmul2_rn(q, x);
+    const float2 pe = __ffma2_rn(q, x, make_float2(-p.x, -p.y));
+    float2 t;
+    acc.hi = two_sum2(acc.hi, p, t);
+    acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(t, pe));
+}
+
 __device__ __forceinline__ DF df_add(DF a, DF b) {
     float e;
     float s = two_sum(a.hi, b.hi, e);

@@ -386,10 +386,30 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
         const uint8_t* rowp = w.stage + srow * stage_stride(row_bytes);
         const float sc = DT == 2 ? __ldg(scales + w.cand[cand_off + srow]) : 1.0f;
         DF acc{0.0f, 0.0f};
+        if constexpr (DT == 0) {
+            // FP32 rows: elements (0, 1) and (2, 3) of each chunk in the two
+            // halves of packed pairs, the halves added at the end
+            DF2 a2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll 1
-        for (int t = 0; t < F8; ++t) {
-            const int c = mm + 8 * t;
-            exact_chunk<DT, METRIC>(acc, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
+            for (int t = 0; t < F8; ++t) {
+                const int c = mm + 8 * t;
+                const float4 xv = *reinterpret_cast<const float4*>(rowp + c * 16);
+                const float4 qv = *reinterpret_cast<const float4*>(q + c * 4);
+                if (METRIC == 0) {
+                    l2_acc_x2(a2, make_float2(qv.x, qv.y), make_float2(xv.x, xv.y));
+                    l2_acc_x2(a2, make_float2(qv.z, qv.w), make_float2(xv.z, xv.w));
+                } else {
+                    ip_acc_x2(a2, make_float2(qv.x, qv.y), make_float2(xv.x, xv.y));
+                    ip_acc_x2(a2, make_float2(qv.z, qv.w), make_float2(xv.z, xv.w));
+                }
+            }
+            acc = df_add(DF{a2.hi.x, a2.lo.x}, DF{a2.hi.y, a2.lo.y});
+        } else {
+#pragma unroll 1
+            for (int t = 0; t < F8; ++t) {
+                const int c = mm + 8 * t;
+                exact_chunk<DT, METRIC>(acc, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC, sc);
+            }
         }
         acc = df_add(acc, df_shfl_xor(acc, 1));
         acc = df_add(acc, df_shfl_xor(acc, 2));
