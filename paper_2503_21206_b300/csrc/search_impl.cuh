@@ -567,6 +567,41 @@ __device__ __forceinline__ uint64_t place_few(Warp& w, uint64_t key, int nkeep) 
     return out;
 }
 
+// Insert one new key (every lane holds it) into C, the common case once C is
+// full.  Its lower bound comes from two ballots, over the chunk heads C[32 i]
+// and then over the chunk that holds it; a key equal to one in C is dropped.
+// The tail C[p .. Snew - 2] moves up one position, two 32-slot chunks per
+// step from the last: every lane reads its sources before any lane writes,
+// and a step writes no position that a later step reads.
+__device__ __forceinline__ void insert_one(Warp& w, uint64_t key, int ef) {
+    const int lane = w.lane;
+    uint64_t* A = w.pool;
+    const int S = w.S;
+    const int h = lane << 5;
+    const unsigned hb = __ballot_sync(kFull, h < S && (A[h] & ~1ull) < key);   // a prefix: C is sorted
+    int p = 0;
+    if (hb) {
+        const int c = 31 - __clz(hb);
+        const int i = (c << 5) + lane;
+        p = (c << 5) + __popc(__ballot_sync(kFull, i < S && (A[i] & ~1ull) < key));
+    }
+    const int Snew = min(S + 1, ef);
+    if (p >= Snew || (p < S && (A[p] & ~1ull) == key)) return;
+    for (int c = (Snew - 1) >> 5; c >= (p >> 5); c -= 2) {
+        const int i0 = (c << 5) + lane, i1 = i0 - 32;
+        const bool m0 = i0 > p && i0 < Snew, m1 = i1 > p;
+        const uint64_t v0 = m0 ? A[i0 - 1] : 0ull, v1 = m1 ? A[i1 - 1] : 0ull;
+        __syncwarp();
+        if (m0) A[i0] = v0;
+        if (m1) A[i1] = v1;
+    }
+    __syncwarp();
+    if (lane == 0) A[p] = key;
+    __syncwarp();
+    w.S = Snew;
+    if (p < w.lb) w.lb = p;
+}
+
 // Merge nb sorted new keys (lanes 0..nb-1, kKeyEmpty beyond) into C in place.
 // A new key equal to one already in C (same distance and id) is dropped.  Each
 // kept key lands at (its rank among the new keys) + (its lower bound in C);
@@ -593,25 +628,6 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
     const int lo_pos = __reduce_min_sync(kFull, np);
     __syncwarp();
     if (lo_pos >= Snew) return;
-    if (nb2 == 1) {
-        // one new key (the common case once C is full): shift C[lo_pos ..
-        // Snew - 2] up by one position, chunk by chunk from the last; each
-        // chunk's sources lie in the chunk itself or the one below, which is
-        // written only in the next iteration, after the barrier
-        for (int c = (Snew - 1) >> 5; c >= (lo_pos >> 5); --c) {
-            const int i = (c << 5) + lane;
-            const bool mv = i > lo_pos && i < Snew;
-            const uint64_t v = mv ? A[i - 1] : 0ull;
-            __syncwarp();
-            if (mv) A[i] = v;
-        }
-        __syncwarp();
-        if (mine) A[lo_pos] = key;
-        __syncwarp();
-        w.S = Snew;
-        if (lo_pos < w.lb) w.lb = lo_pos;
-        return;
-    }
     // two 32-position chunks per step, from the last one down
     const int c_lo = lo_pos >> 5;
     const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
@@ -815,8 +831,13 @@ struct Searcher {
             __syncwarp();
             uint64_t k = lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
             if (k >= worst) k = kKeyEmpty;
-            const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
+            const unsigned km = __ballot_sync(kFull, k != kKeyEmpty);
+            const int nkeep = __popc(km);
             if (nkeep == 0) continue;
+            if (nkeep == 1) {
+                insert_one(w, __shfl_sync(kFull, k, __ffs(km) - 1), w.ef);
+                continue;
+            }
             k = nkeep <= 8 ? place_few(w, k, nkeep) : warp_sort32(k, lane);
             merge_new(w, k, nkeep, w.ef);
         }
