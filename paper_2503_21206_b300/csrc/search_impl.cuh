@@ -568,7 +568,8 @@ __device__ __forceinline__ uint64_t place_few(Warp& w, uint64_t key, int nkeep) 
 }
 
 // Insert one new key (every lane holds it) into C, the common case once C is
-// full.  Its lower bound comes from two ballots, over the chunk heads C[32 i]
+// full (a few keys are inserted one at a time: C stays sorted and keeps the ef
+// best of the union, as the merge does).  Its lower bound comes from two ballots, over the chunk heads C[32 i]
 // and then over the chunk that holds it; a key equal to one in C is dropped.
 // The tail C[p .. Snew - 2] moves up one position, two 32-slot chunks per
 // step from the last: every lane reads its sources before any lane writes,
@@ -834,8 +835,8 @@ struct Searcher {
             const unsigned km = __ballot_sync(kFull, k != kKeyEmpty);
             const int nkeep = __popc(km);
             if (nkeep == 0) continue;
-            if (nkeep == 1) {
-                insert_one(w, __shfl_sync(kFull, k, __ffs(km) - 1), w.ef);
+            if (nkeep <= 3) {   // a few keys: one insertion each, cheaper than sorting and merging
+                for (unsigned rem = km; rem; rem &= rem - 1) insert_one(w, __shfl_sync(kFull, k, __ffs(rem) - 1), w.ef);
                 continue;
             }
             k = nkeep <= 8 ? place_few(w, k, nkeep) : warp_sort32(k, lane);
