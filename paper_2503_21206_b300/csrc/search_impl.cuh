@@ -58,16 +58,22 @@ __host__ __device__ inline int pow2_ceil(int x) {
     return p;
 }
 
+// Per-warp shared memory: the fixed-size scratch arrays first, at constant
+// offsets from the warp's base (so that addressing them needs no registers of
+// their own), then the candidate list, the query rows and the staging buffer.
+constexpr int kOffCand = 0, kOffDist = kCand * 4, kOffSel = kCand * 8, kOffBkeys = kCand * 12,
+              kOffBar = kCand * 20, kOffPool = kCand * 20 + 16;
+
 __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchConfig& cfg) {
     Layout L;
     L.pool_cap = pow2_ceil(cfg.ef < 32 ? 32 : cfg.ef);
-    int o = 0;
-    L.off_pool0 = o; o += L.pool_cap * 8;
-    L.off_cand = o; o += kCand * 4;
-    L.off_dist = o; o += kCand * 4;
-    L.off_bar = o; o += 16;
-    L.off_sel = o; o += kCand * 4;
-    L.off_bkeys = o; o += kCand * 8;
+    int o = kOffPool + L.pool_cap * 8;
+    L.off_pool0 = kOffPool;
+    L.off_cand = kOffCand;
+    L.off_dist = kOffDist;
+    L.off_bar = kOffBar;
+    L.off_sel = kOffSel;
+    L.off_bkeys = kOffBkeys;
     o = round_up(o, 16);
     L.off_q = o; o += ix.d_pad * 4;
     L.off_qp = o; o += ix.qp_pad * 4;
@@ -78,16 +84,18 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
 }
 
 struct Warp {
-    uint64_t* pool;
+    uint8_t* base;       // this warp's slice of shared memory
+    __device__ __forceinline__ uint64_t* pool() const { return reinterpret_cast<uint64_t*>(base + kOffPool); }
+    __device__ __forceinline__ int32_t* cand() const { return reinterpret_cast<int32_t*>(base + kOffCand); }
+    __device__ __forceinline__ int32_t* sel() const { return reinterpret_cast<int32_t*>(base + kOffSel); }
+    __device__ __forceinline__ float* dist() const { return reinterpret_cast<float*>(base + kOffDist); }
+    __device__ __forceinline__ uint64_t* bkeys() const { return reinterpret_cast<uint64_t*>(base + kOffBkeys); }
+    __device__ __forceinline__ uint64_t* bar() const { return reinterpret_cast<uint64_t*>(base + kOffBar); }
     uint16_t* vis;       // this warp slot's visited table
     uint32_t vis_mask;   // buckets in use - 1
     int vis_qbits;       // quotient bits of an entry
     int id_bits;
     int overflow;        // insertions that found no room (visited again if met again)
-    int32_t* cand;
-    int32_t* sel;        // staged rows that need an exact distance
-    float* dist;
-    uint64_t* bkeys;
     float* q;
     float* qp;
     uint8_t* stage;
@@ -97,7 +105,6 @@ struct Warp {
     uint32_t epoch_ctr;
     uint32_t epoch;  // 1..kVisEpochs: the current set's bucket-header tag
     int lane;
-    uint64_t* bar;      // mbarrier of this warp's row gathers
     const uint8_t* red_base;   // the reduced rows (kept in L2 by a cache policy)
     uint32_t phase;     // parity of the barrier phase being waited for
     bool failed;        // a gather did not complete within kMaxPolls polls
@@ -331,7 +338,7 @@ __device__ __forceinline__ void approx_chunk(float2& a, float& b, uint4 v, const
     }
 }
 
-// Keep flags of staged rows rows(0..m-1): w.sel[i] = 0 when row rows(i)'s
+// Keep flags of staged rows rows(0..m-1): w.sel()[i] = 0 when row rows(i)'s
 // certified lower bound exceeds thr (it cannot enter C), else 1.  One row per
 // lane: lane i sums its whole row (the staging stride keeps the lanes' chunks
 // in distinct banks), so no shuffle is needed; cand[cand_off + row] is the
@@ -357,12 +364,12 @@ __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float*
     if (METRIC == 0) {
         lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
     } else if (DT == 2) {
-        const float sc = __ldg(scales + w.cand[cand_off + row]);
+        const float sc = __ldg(scales + w.cand()[cand_off + row]);
         lb = __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
     } else {
         lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
     }
-    w.sel[i] = lb > thr ? 0 : 1;
+    w.sel()[i] = lb > thr ? 0 : 1;
 }
 
 // Exact distances of the staged rows sel(i), i < m, into dist[sel(i)].
@@ -384,7 +391,7 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
         const bool ok = i < m;
         const int srow = sel(ok ? i : 0);
         const uint8_t* rowp = w.stage + srow * stage_stride(row_bytes);
-        const float sc = DT == 2 ? __ldg(scales + w.cand[cand_off + srow]) : 1.0f;
+        const float sc = DT == 2 ? __ldg(scales + w.cand()[cand_off + srow]) : 1.0f;
         DF acc{0.0f, 0.0f};
         if constexpr (DT == 0) {
             // FP32 rows: elements (0, 1) and (2, 3) of each chunk in the two
@@ -420,7 +427,7 @@ __device__ __forceinline__ void exact_staged(Warp& w, int row_bytes, const float
             const float p = two_prod(acc.hi, sc, e);
             acc = DF{p, __fmaf_rn(acc.lo, sc, e)};
         }
-        if (ok && mm == 0) w.dist[cand_off + srow] = df_finish(acc, METRIC);
+        if (ok && mm == 0) w.dist()[cand_off + srow] = df_finish(acc, METRIC);
     }
 }
 
@@ -466,20 +473,20 @@ __device__ __forceinline__ void gather_issue(Warp& w, const uint8_t* __restrict_
                                              int n) {
     fence_proxy_async_smem();
     __syncwarp();
-    if (w.lane == 0) mbar_arrive_expect_tx(w.bar, uint32_t(n * row_bytes));
+    if (w.lane == 0) mbar_arrive_expect_tx(w.bar(), uint32_t(n * row_bytes));
     __syncwarp();
     if (w.lane < n) {
         // reduced rows (small, reused across queries) stay in L2; full rows stream
         const uint64_t pol = base == w.red_base ? l2_evict_last_policy() : l2_evict_first_policy();
         bulk_copy_g2s_hint(w.stage + w.lane * stage_stride(row_bytes),
-                           base + int64_t(w.cand[r0 + w.lane]) * row_bytes, uint32_t(row_bytes), w.bar, pol);
+                           base + int64_t(w.cand()[r0 + w.lane]) * row_bytes, uint32_t(row_bytes), w.bar(), pol);
     }
 }
 
 __device__ __forceinline__ void gather_wait(Warp& w) {
-    if (!mbar_wait(w.bar, w.phase, kMaxPolls)) {
+    if (!mbar_wait(w.bar(), w.phase, kMaxPolls)) {
         // give the copies still in flight one more bounded wait, then report
-        mbar_wait(w.bar, w.phase, kMaxPolls);
+        mbar_wait(w.bar(), w.phase, kMaxPolls);
         w.failed = true;
     }
     w.phase ^= 1u;
@@ -490,7 +497,7 @@ __device__ __forceinline__ void gather_rows(Warp& w, const uint8_t* __restrict__
                                             bool plain) {
     const int n = r1 - r0;
     if (plain) {   // host memory: out of line, off the device-resident path
-        gather_rows_plain(w.stage, base, row_bytes, w.cand + r0, n, w.lane);
+        gather_rows_plain(w.stage, base, row_bytes, w.cand() + r0, n, w.lane);
         return;
     }
     gather_issue(w, base, row_bytes, r0, n);
@@ -535,16 +542,16 @@ __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict
         if (filter) {
             approx_keep<DT, METRIC>(w, row_bytes, scales, q, nr, r0, n_elems, thr, [](int i) { return i; });
             __syncwarp();
-            keep = keep && w.sel[w.lane] != 0;
+            keep = keep && w.sel()[w.lane] != 0;
             __syncwarp();
         }
-        // staged rows still to score exactly, listed in w.sel
+        // staged rows still to score exactly, listed in w.sel()
         const unsigned km = __ballot_sync(kFull, keep);
-        if (keep) w.sel[__popc(km & lanemask_lt())] = w.lane;
-        else if (w.lane < nr) w.dist[r0 + w.lane] = INFINITY;
+        if (keep) w.sel()[__popc(km & lanemask_lt())] = w.lane;
+        else if (w.lane < nr) w.dist()[r0 + w.lane] = INFINITY;
         __syncwarp();
         const int m2 = __popc(km);
-        if (m2 > 0) exact_staged<DT, METRIC>(w, row_bytes, scales, q, m2, [&](int i) { return w.sel[i]; }, r0);
+        if (m2 > 0) exact_staged<DT, METRIC>(w, row_bytes, scales, q, m2, [&](int i) { return w.sel()[i]; }, r0);
         __syncwarp();
     }
 }
@@ -555,14 +562,14 @@ __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict
 __device__ __forceinline__ uint64_t place_few(Warp& w, uint64_t key, int nkeep) {
     const bool has = key != kKeyEmpty;
     const unsigned hm = __ballot_sync(kFull, has);
-    if (has) w.bkeys[__popc(hm & lanemask_lt())] = key;
+    if (has) w.bkeys()[__popc(hm & lanemask_lt())] = key;
     __syncwarp();
     int rank = 0;
-    for (int j = 0; j < nkeep; ++j) rank += w.bkeys[j] < key;
+    for (int j = 0; j < nkeep; ++j) rank += w.bkeys()[j] < key;
     __syncwarp();
-    if (has) w.bkeys[rank] = key;
+    if (has) w.bkeys()[rank] = key;
     __syncwarp();
-    const uint64_t out = w.lane < nkeep ? w.bkeys[w.lane] : kKeyEmpty;
+    const uint64_t out = w.lane < nkeep ? w.bkeys()[w.lane] : kKeyEmpty;
     __syncwarp();
     return out;
 }
@@ -576,7 +583,7 @@ __device__ __forceinline__ uint64_t place_few(Warp& w, uint64_t key, int nkeep) 
 // and a step writes no position that a later step reads.
 __device__ __forceinline__ void insert_one(Warp& w, uint64_t key, int ef) {
     const int lane = w.lane;
-    uint64_t* A = w.pool;
+    uint64_t* A = w.pool();
     const int S = w.S;
     const int h = lane << 5;
     const unsigned hb = __ballot_sync(kFull, h < S && (A[h] & ~1ull) < key);   // a prefix: C is sorted
@@ -611,7 +618,7 @@ __device__ __forceinline__ void insert_one(Warp& w, uint64_t key, int ef) {
 // element is always read before it is overwritten.  C keeps its ef best.
 __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef) {
     const int lane = w.lane;
-    uint64_t* A = w.pool;
+    uint64_t* A = w.pool();
     const int S = w.S;
     // lower bound of every new key in C, in lock step (fixed step count)
     int p = 0;
@@ -624,7 +631,7 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
     if (nb2 == 0) return;
     const int ci = __popc(keep & lanemask_lt());
     const int np = mine ? p + ci : 0x7FFFFFFF;
-    if (mine) w.bkeys[ci] = key;
+    if (mine) w.bkeys()[ci] = key;
     const int Snew = min(S + nb2, ef);
     const int lo_pos = __reduce_min_sync(kFull, np);
     __syncwarp();
@@ -647,11 +654,11 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
         uint64_t v0 = 0, v1 = 0;
         if (wr0) {
             const int kle = before0 + __popc(m0 & upto);
-            v0 = ((m0 >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos0 - kle];
+            v0 = ((m0 >> lane) & 1u) ? w.bkeys()[kle - 1] : A[pos0 - kle];
         }
         if (wr1) {
             const int kle = before1 + __popc(m1 & upto);
-            v1 = ((m1 >> lane) & 1u) ? w.bkeys[kle - 1] : A[pos1 - kle];
+            v1 = ((m1 >> lane) & 1u) ? w.bkeys()[kle - 1] : A[pos1 - kle];
         }
         __syncwarp();
         if (wr0) A[pos0] = v0;
@@ -664,7 +671,7 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
 
 // Ascending bitonic sort of C in place (the re-rank), padded to a power of two.
 __device__ __forceinline__ void sort_pool(Warp& w, int cap) {
-    uint64_t* A = w.pool;
+    uint64_t* A = w.pool();
     int N = 1;
     while (N < w.S) N <<= 1;
     for (int i = w.S + w.lane; i < N && i < cap; i += 32) A[i] = kKeyEmpty;
@@ -762,7 +769,7 @@ struct Searcher {
         int idx = -1, idx2 = -1;
         for (int b0 = w.lb; b0 < w.S; b0 += 32) {
             const int i = b0 + lane;
-            const bool unc = i < w.S && !(w.pool[i] & 1ull);
+            const bool unc = i < w.S && !(w.pool()[i] & 1ull);
             const unsigned b = __ballot_sync(kFull, unc);
             if (b) {
                 idx = b0 + __ffs(b) - 1;
@@ -775,9 +782,9 @@ struct Searcher {
             w.lb = w.S;
             return false;
         }
-        const uint64_t key = w.pool[idx];
+        const uint64_t key = w.pool()[idx];
         __syncwarp();
-        if (lane == 0) w.pool[idx] = key | 1ull;
+        if (lane == 0) w.pool()[idx] = key | 1ull;
         w.lb = idx + 1;
         n_exp += 1;
         const int32_t u = key_id(key);
@@ -789,7 +796,7 @@ struct Searcher {
         // cost more DRAM traffic than it saved: the guess is wrong about 40%
         // of the time)
         if (idx2 >= 0) {
-            const int32_t* r2 = adjacency(view, key_id(w.pool[idx2]));
+            const int32_t* r2 = adjacency(view, key_id(w.pool()[idx2]));
             if (r2) {
                 const uintptr_t first = reinterpret_cast<uintptr_t>(r2) >> 7;
                 const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + (view == 3 ? ix.R : ix.R_sub)) - 1) >> 7;
@@ -809,14 +816,14 @@ struct Searcher {
             const bool isnew = visit(w, v, v >= 0);
             const unsigned nb = __ballot_sync(kFull, isnew);
             const int m = __popc(nb);
-            if (isnew) w.cand[__popc(nb & lanemask_lt())] = v;
+            if (isnew) w.cand()[__popc(nb & lanemask_lt())] = v;
             __syncwarp();
             n_dist += m;
             if (m == 0) continue;
             // a full list only admits keys below its worst one: rows certified
             // above its distance are not scored exactly
             const bool full = w.S == w.ef;
-            const uint64_t worst = full ? (w.pool[w.S - 1] & ~1ull) : kKeyEmpty;
+            const uint64_t worst = full ? (w.pool()[w.S - 1] & ~1ull) : kKeyEmpty;
             const uint32_t wbits = uint32_t(worst >> 32);
             const bool filter = full && cfg.filter && wbits != orderable(INFINITY);
             const float thr = filter ? from_orderable(wbits + 1u) : INFINITY;   // nextup(worst distance)
@@ -830,7 +837,7 @@ struct Searcher {
                 reduced_expand_batch(m, filter, thr);
             }
             __syncwarp();
-            uint64_t k = lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
+            uint64_t k = lane < m ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty;
             if (k >= worst) k = kKeyEmpty;
             const unsigned km = __ballot_sync(kFull, k != kKeyEmpty);
             const int nkeep = __popc(km);
@@ -874,25 +881,25 @@ struct Searcher {
             const bool valid = p >= 0 && p < ix.n_entry;
             const unsigned vb = __ballot_sync(kFull, valid);
             const int m = __popc(vb);
-            if (valid) w.cand[__popc(vb & lanemask_lt())] = __ldg(ix.entry + p);
+            if (valid) w.cand()[__popc(vb & lanemask_lt())] = __ldg(ix.entry + p);
             __syncwarp();
             reduced_batch(m);
             __syncwarp();
-            const uint64_t key = warp_sort32(lane < m ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
+            const uint64_t key = warp_sort32(lane < m ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty, lane);
             const uint64_t kth = __shfl_sync(kFull, key, ns - 1);
             if (m >= ns && fes_lb >= double(nextafterf(key_dist(kth), INFINITY))) {
-                if (lane < ns) w.pool[lane] = key;
+                if (lane < ns) w.pool()[lane] = key;
                 w.S = ns;
             } else {
                 scan = true;
             }
         } else if (cfg.use_fes == 0) {
-            if (lane < ns) w.cand[lane] = __ldg(ix.entry + lane);
+            if (lane < ns) w.cand()[lane] = __ldg(ix.entry + lane);
             __syncwarp();
             reduced_batch(ns);
             __syncwarp();
-            const uint64_t key = warp_sort32(lane < ns ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty, lane);
-            if (lane < ns) w.pool[lane] = key;
+            const uint64_t key = warp_sort32(lane < ns ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty, lane);
+            if (lane < ns) w.pool()[lane] = key;
             w.S = ns;
         }
         const int32_t* scan_list = ix.entry;   // entries scanned exactly, if any
@@ -903,12 +910,12 @@ struct Searcher {
             uint64_t bestc = kKeyEmpty;
             for (int c0 = 0; c0 < ix.n_clusters; c0 += kCand) {
                 const int mm = ix.n_clusters - c0 < kCand ? ix.n_clusters - c0 : kCand;
-                if (lane < mm) w.cand[lane] = c0 + lane;
+                if (lane < mm) w.cand()[lane] = c0 + lane;
                 __syncwarp();
                 batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.centroids), ix.cent_pad * 4, nullptr,
                                       w.qp, mm, cfg.stage_bytes, false);
                 __syncwarp();
-                const uint64_t k = warp_min_key(lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty);
+                const uint64_t k = warp_min_key(lane < mm ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty);
                 bestc = k < bestc ? k : bestc;
                 __syncwarp();
             }
@@ -925,12 +932,12 @@ struct Searcher {
             w.ef = ns;
             for (int64_t e0 = 0; e0 < scan_count; e0 += kCand) {
                 const int mm = scan_count - e0 < kCand ? int(scan_count - e0) : kCand;
-                if (lane < mm) w.cand[lane] = __ldg(scan_list + e0 + lane);
+                if (lane < mm) w.cand()[lane] = __ldg(scan_list + e0 + lane);
                 __syncwarp();
                 reduced_batch(mm);
                 __syncwarp();
-                uint64_t k = lane < mm ? make_key(w.dist[lane], w.cand[lane]) : kKeyEmpty;
-                if (w.S == w.ef && k >= w.pool[w.S - 1]) k = kKeyEmpty;
+                uint64_t k = lane < mm ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty;
+                if (w.S == w.ef && k >= w.pool()[w.S - 1]) k = kKeyEmpty;
                 const int nkeep = __popc(__ballot_sync(kFull, k != kKeyEmpty));
                 if (nkeep > 0) {
                     k = warp_sort32(k, lane);
@@ -941,9 +948,9 @@ struct Searcher {
             w.ef = ef_keep;
         }
         __syncwarp();
-        st.best = w.pool[0];
+        st.best = w.pool()[0];
         // stage (1) starts from the seeds, all unchecked; visited = the seeds
-        visit(w, lane < w.S ? key_id(w.pool[lane]) : 0, lane < w.S);
+        visit(w, lane < w.S ? key_id(w.pool()[lane]) : 0, lane < w.S);
         w.lb = 0;
         st.phase = kStage1;
         st.it = 0;
@@ -959,14 +966,14 @@ struct Searcher {
             const int m = min(kCand, w.S - b0);
             int32_t orig = -1;
             if (lane < m) {
-                orig = __ldg(ix.sub2full + key_id(w.pool[b0 + lane]));
+                orig = __ldg(ix.sub2full + key_id(w.pool()[b0 + lane]));
                 PILOT_CHECK_INDEX(w, orig, ix.n);
-                w.cand[lane] = orig < 0 ? 0 : orig;
+                w.cand()[lane] = orig < 0 ? 0 : orig;
             }
             __syncwarp();
             full_batch(m);
             __syncwarp();
-            if (lane < m) w.pool[b0 + lane] = make_key(w.dist[lane], orig);
+            if (lane < m) w.pool()[b0 + lane] = make_key(w.dist()[lane], orig);
             visit(w, orig, orig >= 0);
             __syncwarp();
         }
@@ -989,13 +996,13 @@ struct Searcher {
             const unsigned vb = __ballot_sync(kFull, v >= 0);
             const int m = __popc(vb);
             if (m == 0) continue;
-            if (v >= 0) w.cand[__popc(vb & lanemask_lt())] = v;
+            if (v >= 0) w.cand()[__popc(vb & lanemask_lt())] = v;
             __syncwarp();
             full_batch(m);
             __syncwarp();
             uint64_t k = kKeyEmpty;
-            if (lane < m) k = make_key(w.dist[lane], w.cand[lane]);
-            visit(w, lane < m ? w.cand[lane] : 0, lane < m);
+            if (lane < m) k = make_key(w.dist()[lane], w.cand()[lane]);
+            visit(w, lane < m ? w.cand()[lane] : 0, lane < m);
             scored += m;
             k = warp_sort32(k, lane);
             merge_new(w, k, m, w.ef);
@@ -1032,7 +1039,7 @@ struct Searcher {
             } else if (st.phase == kStage2) {
                 if (st.it >= cfg.stage2_expansions || !expand(2, st.e2, st.d2)) {
                     if (cfg.stage3) {   // stage (3): every candidate unchecked on the full graph
-                        for (int i = w.lane; i < w.S; i += 32) w.pool[i] &= ~1ull;
+                        for (int i = w.lane; i < w.S; i += 32) w.pool()[i] &= ~1ull;
                         w.lb = 0;
                         __syncwarp();
                         st.phase = kStage3;
@@ -1062,7 +1069,7 @@ struct Searcher {
     __device__ void write_output(const QState& st, int k, int32_t* ids, float* dists, int32_t* counters) {
         for (int j = w.lane; j < k; j += 32) {
             const bool ok = j < w.S && !w.failed;
-            const uint64_t kk = ok ? w.pool[j] : kKeyEmpty;
+            const uint64_t kk = ok ? w.pool()[j] : kKeyEmpty;
             ids[j] = ok ? key_id(kk) : -1;
             dists[j] = ok ? key_dist(kk) : INFINITY;
         }
@@ -1096,12 +1103,7 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     const int warp = threadIdx.x >> 5;
     uint8_t* base = smem + size_t(warp) * L.per_warp;
     Warp w;
-    w.pool = reinterpret_cast<uint64_t*>(base + L.off_pool0);
-    w.cand = reinterpret_cast<int32_t*>(base + L.off_cand);
-    w.dist = reinterpret_cast<float*>(base + L.off_dist);
-    w.sel = reinterpret_cast<int32_t*>(base + L.off_sel);
-    w.bar = reinterpret_cast<uint64_t*>(base + L.off_bar);
-    w.bkeys = reinterpret_cast<uint64_t*>(base + L.off_bkeys);
+    w.base = base;
     w.q = reinterpret_cast<float*>(base + L.off_q);
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
     w.stage = base + L.off_stage;
@@ -1119,7 +1121,7 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     w.vis_qbits = cfg.vis_qbits;
     w.id_bits = ix.id_bits;
     w.overflow = 0;
-    if (w.lane == 0) mbar_init(w.bar, 1);
+    if (w.lane == 0) mbar_init(w.bar(), 1);
     __syncwarp();
     return w;
 }
@@ -1219,7 +1221,7 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
             const VisSize vs = vis_size_for(w.ef, ix.R > ix.R_sub ? ix.R : ix.R_sub, ix.id_bits, ix.vis_stride);
             w.vis_mask = vs.mask;
             w.vis_qbits = vs.qbits;
-            for (int j = w.lane; j < w.S; j += 32) w.pool[j] = gpool[j];
+            for (int j = w.lane; j < w.S; j += 32) w.pool()[j] = gpool[j];
             __syncwarp();
         }
         s.advance(st, sio.budget);
@@ -1234,7 +1236,7 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
                 sio.res_done[e.slot] = w.failed ? 2 : 1;
             }
         } else {
-            for (int j = w.lane; j < w.S; j += 32) gpool[j] = w.pool[j];
+            for (int j = w.lane; j < w.S; j += 32) gpool[j] = w.pool()[j];
             if (w.lane == 0) {
                 ss->phase = st.phase; ss->it = st.it;
                 ss->e1 = st.e1; ss->d1 = st.d1; ss->e2 = st.e2; ss->d2 = st.d2; ss->e3 = st.e3; ss->d3 = st.d3;
