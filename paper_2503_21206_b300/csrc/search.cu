@@ -43,13 +43,13 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.fes_T = kFesT;
     cfg.fes_seeds = 1;
     cfg.warps_per_block = 2;
-    // 20 rows of the widest kind per gather pass (an expansion probes its
+    // 24 rows of the widest kind per gather pass (an expansion probes its
     // neighbours first and gathers only the unvisited ones, typically fewer
     // than 24 of 32), at most ~16.5 KB, at least 4 wide or 32 reduced rows
     const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
     int stage = 4 * (fs > rs ? fs : rs);
-    const int full20 = 20 * fs < 16896 ? 20 * fs : 16896;
-    stage = stage > full20 ? stage : full20;
+    const int full24 = 24 * fs < 16896 ? 24 * fs : 16896;
+    stage = stage > full24 ? stage : full24;
     cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
     cfg.filter = 1;
     set_visited_size(ix, cfg, ix.vis_stride);

@@ -45,7 +45,7 @@ constexpr int kMaxExpansionsPerStage = 1 << 22;
 constexpr uint32_t kMaxPolls = 1u << 24;   // bound on polls of one gather's barrier
 
 struct Layout {
-    int pool_cap;      // power of two >= ef
+    int pool_cap;      // keys C can hold: ef rounded up to a multiple of 32 (at least 32)
     int off_pool0, off_cand, off_dist, off_bar, off_sel, off_bkeys, off_q, off_qp, off_stage;
     int per_warp;
 };
@@ -66,7 +66,7 @@ constexpr int kOffCand = 0, kOffDist = kCand * 4, kOffSel = kCand * 8, kOffBkeys
 
 __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchConfig& cfg) {
     Layout L;
-    L.pool_cap = pow2_ceil(cfg.ef < 32 ? 32 : cfg.ef);
+    L.pool_cap = round_up(cfg.ef < 32 ? 32 : cfg.ef, 32);
     int o = kOffPool + L.pool_cap * 8;
     L.off_pool0 = kOffPool;
     L.off_cand = kOffCand;
@@ -669,21 +669,25 @@ __device__ __forceinline__ void merge_new(Warp& w, uint64_t key, int nb, int ef)
     if (lo_pos < w.lb) w.lb = lo_pos;
 }
 
-// Ascending bitonic sort of C in place (the re-rank), padded to a power of two.
-__device__ __forceinline__ void sort_pool(Warp& w, int cap) {
+// Ascending sort of C's S keys in place (the re-rank): a bitonic network
+// over the next power of two N >= S in the form whose compare-exchanges all
+// put the smaller key first (the first step of each merge pairs i with its
+// mirror i ^ (k - 1)), so the positions past S can stand for +inf without
+// being stored: a pair reaching past S never swaps.  C needs no more room
+// than S keys.
+__device__ __forceinline__ void sort_pool(Warp& w) {
     uint64_t* A = w.pool();
+    const int S = w.S;
     int N = 1;
-    while (N < w.S) N <<= 1;
-    for (int i = w.S + w.lane; i < N && i < cap; i += 32) A[i] = kKeyEmpty;
-    __syncwarp();
+    while (N < S) N <<= 1;
     for (int k = 2; k <= N; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = w.lane; i < N; i += 32) {
-                const int l = i ^ j;
-                if (l > i) {
-                    uint64_t a = A[i], b = A[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
+            const int x = j == (k >> 1) ? k - 1 : j;
+            for (int i = w.lane; i < S; i += 32) {
+                const int l = i ^ x;
+                if (l > i && l < S) {
+                    const uint64_t a = A[i], b = A[l];
+                    if (a > b) {
                         A[i] = b;
                         A[l] = a;
                     }
@@ -977,7 +981,7 @@ struct Searcher {
             visit(w, orig, orig >= 0);
             __syncwarp();
         }
-        sort_pool(w, 0x7FFFFFFF);
+        sort_pool(w);
         w.lb = 0;
     }
 
