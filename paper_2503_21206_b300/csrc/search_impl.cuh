@@ -343,15 +343,12 @@ __device__ __forceinline__ void approx_chunk(float2& a, float& b, uint4 v, const
 // lane: lane i sums its whole row (the staging stride keeps the lanes' chunks
 // in distinct banks), so no shuffle is needed; cand[cand_off + row] is the
 // row's id (for the FP8 scale).  The caller synchronises the warp afterwards.
-template <int DT, int METRIC, class Rows>
-__device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float* __restrict__ scales,
-                                            const float* q, int m, int cand_off, int n_elems, float thr,
-                                            Rows rows) {
-    const int i = w.lane;
-    if (i >= m) return;
+// Certified lower bound on the exact distance of one staged row (rowp, n_elems
+// elements); sc is the row's FP8 scale (inner product only).
+template <int DT, int METRIC>
+__device__ __forceinline__ float approx_lb(const uint8_t* rowp, int row_bytes, const float* q, int n_elems,
+                                           const float* __restrict__ sc_ptr) {
     constexpr int EPC = DT == 0 ? 4 : (DT == 1 ? 8 : 16);
-    const int row = rows(i);   // the staged row lane i tests
-    const uint8_t* rowp = w.stage + row * stage_stride(row_bytes);
     const int nch = row_bytes >> 4;
     float2 a = make_float2(0.0f, 0.0f);
     float b = 0.0f;
@@ -360,15 +357,23 @@ __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float*
         approx_chunk<DT, METRIC>(a, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * EPC);
     const float A = __fadd_rn(a.x, a.y);
     const float rel = float(n_elems + 8) * 1.1920928955078125e-7f;   // 2 (n + 8) u, u = 2^-24
-    float lb;
-    if (METRIC == 0) {
-        lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
-    } else if (DT == 2) {
-        const float sc = __ldg(scales + w.cand()[cand_off + row]);
-        lb = __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
-    } else {
-        lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
+    if (METRIC == 0) return __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
+    if (DT == 2) {
+        const float sc = __ldg(sc_ptr);
+        return __fsub_rd(-__fmul_ru(sc, __fmaf_ru(rel, b, A)), kTiny);
     }
+    return __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
+}
+
+template <int DT, int METRIC, class Rows>
+__device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float* __restrict__ scales,
+                                            const float* q, int m, int cand_off, int n_elems, float thr,
+                                            Rows rows) {
+    const int i = w.lane;
+    if (i >= m) return;
+    const int row = rows(i);   // the staged row lane i tests
+    const float lb = approx_lb<DT, METRIC>(w.stage + row * stage_stride(row_bytes), row_bytes, q, n_elems,
+                                           DT == 2 ? scales + w.cand()[cand_off + row] : nullptr);
     w.sel()[i] = lb > thr ? 0 : 1;
 }
 
@@ -481,6 +486,20 @@ __device__ __forceinline__ void gather_issue(Warp& w, const uint8_t* __restrict_
         bulk_copy_g2s_hint(w.stage + w.lane * stage_stride(row_bytes),
                            base + int64_t(w.cand()[r0 + w.lane]) * row_bytes, uint32_t(row_bytes), w.bar(), pol);
     }
+}
+
+// Copy row v (of `base`, row_bytes each) into staging slot `lane` for every
+// lane with v >= 0 (the lanes of mask vb), completing on the warp's barrier;
+// the rows are kept in L2 (evict_last).  gather_wait waits.
+__device__ __forceinline__ void gather_issue_lanes(Warp& w, const uint8_t* __restrict__ base, int row_bytes, int32_t v,
+                                                   unsigned vb) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (w.lane == 0) mbar_arrive_expect_tx(w.bar(), uint32_t(__popc(vb) * row_bytes));
+    __syncwarp();
+    if (v >= 0)
+        bulk_copy_g2s_hint(w.stage + w.lane * stage_stride(row_bytes), base + int64_t(v) * row_bytes,
+                           uint32_t(row_bytes), w.bar(), l2_evict_last_policy());
 }
 
 __device__ __forceinline__ void gather_wait(Warp& w) {
@@ -747,14 +766,6 @@ struct Searcher {
         batch_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr, w.q, m,
                               cfg.stage_bytes, ix.full_host != 0);
     }
-    // An expansion's new rows, pre-filtered against thr when `filter`.
-    __device__ __forceinline__ void reduced_expand_batch(int m, bool filter, float thr) {
-        // FP8 rows under L2 are always scored exactly (see the pre-filter notes)
-        filtered_dist<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes, ix.red_scales,
-                                  w.qp, m, cfg.stage_bytes, false, filter && !(DT == 2 && METRIC == 0), thr,
-                                  ix.dp_pad);
-    }
-
     // Adjacency row of node u in a view (null if it has none).
     __device__ __forceinline__ const int32_t* adjacency(int view, int32_t u) const {
         if (view == 1) return ix.sub_adj + int64_t(u) * ix.R_sub;
@@ -815,33 +826,62 @@ struct Searcher {
             PILOT_CHECK_INDEX(w, v, view == 3 ? ix.n : ix.n_sub);
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
             PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
-            // the visited probe comes first: only unvisited neighbours are
-            // gathered and scored
-            const bool isnew = visit(w, v, v >= 0);
-            const unsigned nb = __ballot_sync(kFull, isnew);
-            const int m = __popc(nb);
-            if (isnew) w.cand()[__popc(nb & lanemask_lt())] = v;
-            __syncwarp();
-            n_dist += m;
-            if (m == 0) continue;
-            // a full list only admits keys below its worst one: rows certified
-            // above its distance are not scored exactly
-            const bool full = w.S == w.ef;
-            const uint64_t worst = full ? (w.pool()[w.S - 1] & ~1ull) : kKeyEmpty;
-            const uint32_t wbits = uint32_t(worst >> 32);
-            const bool filter = full && cfg.filter && wbits != orderable(INFINITY);
-            const float thr = filter ? from_orderable(wbits + 1u) : INFINITY;   // nextup(worst distance)
-            if (DT == 0 || view != 1) {   // one call site for both row kinds when they share a type
-                const bool red = view == 1;
-                filtered_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(red ? ix.red : ix.full),
-                                         red ? ix.red_row_bytes : ix.full_row_bytes, nullptr, red ? w.qp : w.q,
-                                         m, cfg.stage_bytes, !red && ix.full_host != 0, filter, thr,
-                                         red ? ix.dp_pad : ix.d_pad);
+            uint64_t k = kKeyEmpty, worst = kKeyEmpty;
+            if (view == 1) {
+                // stage (1): every neighbour's reduced row is copied into
+                // staging slot `lane` while its visited bucket is probed, so
+                // that the two round trips overlap; the rows of neighbours
+                // found visited are copied but never read (reduced rows are
+                // small, and kept in L2)
+                w.cand()[lane] = v;
+                const unsigned vb = __ballot_sync(kFull, v >= 0);
+                if (vb) gather_issue_lanes(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes, v, vb);
+                const bool isnew = visit(w, v, v >= 0);
+                const int m = __popc(__ballot_sync(kFull, isnew));
+                n_dist += m;
+                if (vb) gather_wait(w);
+                if (m == 0) continue;
+                const bool full = w.S == w.ef;
+                worst = full ? (w.pool()[w.S - 1] & ~1ull) : kKeyEmpty;
+                const uint32_t wbits = uint32_t(worst >> 32);
+                // FP8 rows under L2 are always scored exactly (see the pre-filter notes)
+                const bool filter = full && cfg.filter && wbits != orderable(INFINITY) && !(DT == 2 && METRIC == 0);
+                bool keep = isnew;
+                if (filter && isnew)
+                    keep = approx_lb<DT, METRIC>(w.stage + lane * stage_stride(ix.red_row_bytes), ix.red_row_bytes,
+                                                 w.qp, ix.dp_pad, DT == 2 ? ix.red_scales + v : nullptr) <=
+                           from_orderable(wbits + 1u);   // nextup(worst distance)
+                const unsigned kb = __ballot_sync(kFull, keep);
+                if (keep) w.sel()[__popc(kb & lanemask_lt())] = lane;
+                __syncwarp();
+                const int m2 = __popc(kb);
+                if (m2 > 0)
+                    exact_staged<DT, METRIC>(w, ix.red_row_bytes, ix.red_scales, w.qp, m2,
+                                             [&](int i) { return w.sel()[i]; }, 0);
+                __syncwarp();
+                if (keep) k = make_key(w.dist()[lane], v);
             } else {
-                reduced_expand_batch(m, filter, thr);
+                // the visited probe comes first: only unvisited neighbours are
+                // gathered and scored
+                const bool isnew = visit(w, v, v >= 0);
+                const unsigned nb = __ballot_sync(kFull, isnew);
+                const int m = __popc(nb);
+                if (isnew) w.cand()[__popc(nb & lanemask_lt())] = v;
+                __syncwarp();
+                n_dist += m;
+                if (m == 0) continue;
+                // a full list only admits keys below its worst one: rows certified
+                // above its distance are not scored exactly
+                const bool full = w.S == w.ef;
+                worst = full ? (w.pool()[w.S - 1] & ~1ull) : kKeyEmpty;
+                const uint32_t wbits = uint32_t(worst >> 32);
+                const bool filter = full && cfg.filter && wbits != orderable(INFINITY);
+                const float thr = filter ? from_orderable(wbits + 1u) : INFINITY;   // nextup(worst distance)
+                filtered_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr,
+                                         w.q, m, cfg.stage_bytes, ix.full_host != 0, filter, thr, ix.d_pad);
+                __syncwarp();
+                if (lane < m) k = make_key(w.dist()[lane], w.cand()[lane]);
             }
-            __syncwarp();
-            uint64_t k = lane < m ? make_key(w.dist()[lane], w.cand()[lane]) : kKeyEmpty;
             if (k >= worst) k = kKeyEmpty;
             const unsigned km = __ballot_sync(kFull, k != kKeyEmpty);
             const int nkeep = __popc(km);
