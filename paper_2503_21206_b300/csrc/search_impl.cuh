@@ -33,6 +33,7 @@
 #pragma once
 
 #include <cfloat>
+#include <climits>
 
 #include "device_common.cuh"
 #include "kernels.h"
@@ -85,6 +86,8 @@ __host__ __device__ inline Layout make_layout(const DevIndex& ix, const SearchCo
 
 struct Warp {
     uint8_t* base;       // this warp's slice of shared memory
+    int32_t nx_tag;      // whose adjacency row nx_v0 holds: u (view 3), ~u (view 1), INT_MIN none
+    int32_t nx_v0;       // entry `lane` of that row
     __device__ __forceinline__ uint64_t* pool() const { return reinterpret_cast<uint64_t*>(base + kOffPool); }
     __device__ __forceinline__ int32_t* cand() const { return reinterpret_cast<int32_t*>(base + kOffCand); }
     __device__ __forceinline__ int32_t* sel() const { return reinterpret_cast<int32_t*>(base + kOffSel); }
@@ -377,6 +380,42 @@ __device__ __forceinline__ void approx_keep(Warp& w, int row_bytes, const float*
     w.sel()[i] = lb > thr ? 0 : 1;
 }
 
+// Keep flags like approx_keep for FP32 rows, eight lanes per row: lane
+// (g, mm) sums chunks mm + 8 t of staged row g + 4 j, four rows at a time, and
+// a butterfly over the row's eight lanes adds the partial sums (the bound
+// holds for any summation order).  Rows are whole 128-byte lines, so every
+// lane of a row has the same number of chunks.
+template <int METRIC>
+__device__ __forceinline__ void approx_keep8(Warp& w, int row_bytes, const float* q, int m, int n_elems, float thr) {
+    const int g = w.lane >> 3, mm = w.lane & 7;
+    const int nch = row_bytes >> 4;
+    const float rel = float(n_elems + 8) * 1.1920928955078125e-7f;   // 2 (n + 8) u, u = 2^-24
+#pragma unroll 1
+    for (int j = 0; j < ((m + 3) >> 2); ++j) {
+        const int i = g + 4 * j;
+        const uint8_t* rowp = w.stage + (i < m ? i : 0) * stage_stride(row_bytes);
+        float2 a = make_float2(0.0f, 0.0f);
+        float b = 0.0f;
+#pragma unroll 2
+        for (int c = mm; c < nch; c += 8)
+            approx_chunk<0, METRIC>(a, b, *reinterpret_cast<const uint4*>(rowp + c * 16), q + c * 4);
+        float A = __fadd_rn(a.x, a.y);
+        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 1));
+        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 2));
+        A = __fadd_rn(A, __shfl_xor_sync(kFull, A, 4));
+        float lb;
+        if (METRIC == 0) {
+            lb = __fsub_rd(__fmaf_rd(A, -rel, A), kTiny);
+        } else {
+            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 1));
+            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 2));
+            b = __fadd_rn(b, __shfl_xor_sync(kFull, b, 4));
+            lb = __fsub_rd(__fmaf_rd(-rel, b, -A), kTiny);
+        }
+        if (mm == 0 && i < m) w.sel()[i] = lb > thr ? 0 : 1;
+    }
+}
+
 // Exact distances of the staged rows sel(i), i < m, into dist[sel(i)].
 // Staged row s lives at stage + s * stage_stride(row_bytes).  Lane (g, mm) covers chunks
 // mm + 8 t of rows g + 4 j; one row slot j at a time (a warp-uniform loop,
@@ -559,7 +598,14 @@ __device__ __forceinline__ void filtered_dist(Warp& w, const uint8_t* __restrict
         gather_rows(w, base, row_bytes, r0, r1, plain);
         bool keep = w.lane < nr;
         if (filter) {
-            approx_keep<DT, METRIC>(w, row_bytes, scales, q, nr, r0, n_elems, thr, [](int i) { return i; });
+            // one row per lane, or eight lanes per row when a row per lane
+            // would leave most lanes idle (few or long rows): the cost of
+            // each, in chunk steps, is nch against ceil(nr / 4) (nch / 8 + ~1.4)
+            const int nch = row_bytes >> 4;
+            if (DT == 0 && ((nr + 3) >> 2) * (nch + 11) < nch * 8)
+                approx_keep8<METRIC>(w, row_bytes, q, nr, n_elems, thr);
+            else
+                approx_keep<DT, METRIC>(w, row_bytes, scales, q, nr, r0, n_elems, thr, [](int i) { return i; });
             __syncwarp();
             keep = keep && w.sel()[w.lane] != 0;
             __syncwarp();
@@ -805,16 +851,26 @@ struct Searcher {
         const int32_t u = key_id(key);
         const int32_t* row = adjacency(view, u);
         const int W = view == 3 ? ix.R : (row ? ix.R_sub : 0);
-        // the next expansion most likely takes the second unchecked candidate:
-        // bring its adjacency row (every 128-byte line it spans) into L2 while
-        // this one runs (prefetching its neighbours' visited buckets as well
-        // cost more DRAM traffic than it saved: the guess is wrong about 40%
-        // of the time)
+        const uint64_t pol = view == 3 ? l2_evict_first_policy() : l2_evict_last_policy();
+        // The next expansion most likely takes the second unchecked candidate
+        // (the guess fails about 40% of the time): its adjacency row (degree
+        // up to 32) is loaded into a register now and used then if the guess
+        // held, a one-entry cache of (view, node) -> row.  Stage (2), two
+        // expansions reached through full2sub, and wider rows only prefetch
+        // the row into L2.
+        const bool have = view != 2 && W <= 32 && (view == 3 ? u : ~u) == w.nx_tag;
+        const int32_t h0 = w.nx_v0;
+        w.nx_tag = INT_MIN;
         if (idx2 >= 0) {
-            const int32_t* r2 = adjacency(view, key_id(w.pool()[idx2]));
-            if (r2) {
+            const int32_t u2 = key_id(w.pool()[idx2]);
+            const int32_t* r2 = adjacency(view, u2);
+            const int W2 = view == 3 ? ix.R : ix.R_sub;
+            if (view != 2 && W2 <= 32) {
+                w.nx_v0 = lane < W2 ? ld_nc_hint(r2 + lane, pol) : -1;
+                w.nx_tag = view == 3 ? u2 : ~u2;
+            } else if (r2) {
                 const uintptr_t first = reinterpret_cast<uintptr_t>(r2) >> 7;
-                const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + (view == 3 ? ix.R : ix.R_sub)) - 1) >> 7;
+                const uintptr_t last = (reinterpret_cast<uintptr_t>(r2 + W2) - 1) >> 7;
                 if (uintptr_t(lane) <= last - first)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"((first + lane) << 7));
             }
@@ -822,7 +878,8 @@ struct Searcher {
         __syncwarp();
         for (int b0 = 0; b0 < W; b0 += 32) {
             const int j = b0 + lane;
-            int32_t v = j < W ? ld_nc_hint(row + j, view == 3 ? l2_evict_first_policy() : l2_evict_last_policy()) : -1;
+            int32_t v = -1;
+            if (j < W) v = have ? h0 : ld_nc_hint(row + j, pol);
             PILOT_CHECK_INDEX(w, v, view == 3 ? ix.n : ix.n_sub);
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
             PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
@@ -1148,6 +1205,8 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     uint8_t* base = smem + size_t(warp) * L.per_warp;
     Warp w;
     w.base = base;
+    w.nx_tag = INT_MIN;
+    w.nx_v0 = -1;
     w.q = reinterpret_cast<float*>(base + L.off_q);
     w.qp = reinterpret_cast<float*>(base + L.off_qp);
     w.stage = base + L.off_stage;
