@@ -269,6 +269,16 @@ __device__ __forceinline__ int32_t ld_nc_hint(const int32_t* p, uint64_t pol) {
     return v;
 }
 
+// One 32-byte global load (a 256-bit vector access, one instruction instead of
+// two 128-bit ones); p must be 32-byte aligned.  Ordered after earlier stores
+// of the warp by the caller's __syncwarp.
+__device__ __forceinline__ void ld_global_32B(const void* p, uint4& x, uint4& y) {
+    asm volatile("ld.global.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w), "=r"(y.x), "=r"(y.y), "=r"(y.z), "=r"(y.w)
+                 : "l"(p)
+                 : "memory");
+}
+
 // Wait until the barrier completes the phase with the given parity.  Gives up
 // after max_iter polls and returns false (the caller reports an error).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter) {

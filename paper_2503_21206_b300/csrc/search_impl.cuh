@@ -160,7 +160,8 @@ __device__ __forceinline__ bool visit(Warp& w, int32_t v, bool valid) {
         int cnt = 0;
         bool stale = false;
         if (pending) {
-            const uint4 x = *reinterpret_cast<const uint4*>(bp), y = *reinterpret_cast<const uint4*>(bp + 8);
+            uint4 x, y;
+            ld_global_32B(bp, x, y);
             stale = ((x.x & 0xFFFFu) >> 4) != w.epoch;
             if (!stale) {
                 cnt = int(x.x & 15u);
