@@ -266,7 +266,8 @@ pilot_status pilot_search_noalloc(pilot_index* index, const float* queries, int6
  * Admission: ef <= max_ef (the step kernel's shared memory is sized for
  * max_ef; PILOT_EINVAL above it) and k <= max_k; the number of slots is
  * max_slots or what hbm_budget_bytes holds (list, query rows and a visited
- * table of 4 x pow2(1.25 x max_ef x max(R, R_sub)) bytes per slot, independent of n),
+ * table of 2 x pow2(1.25 x max_ef x max(R, R_sub)) bytes per slot, independent of n
+ * below 2^24 rows),
  * whichever is smaller, rounded down to a multiple of the warps the step
  * kernel keeps resident (when it holds at least one such wave); further
  * requests queue, and submit returns PILOT_EBUSY when queue_capacity
@@ -334,9 +335,11 @@ void pilot_serve_destroy(pilot_server* server);
  *   warps_per_block  in {1, 2, 4, 8}   (queries per block; one warp each)
  *   stage_rows       in {8, 12, 16, 20, 24, 32} (rows staged per gather pass)
  * whose shared memory fits, and for the defaults.  The fastest becomes the
- * index's shape for that ef class: pilot_search / pilot_search_ex calls whose
- * options leave warps_per_block or stage_rows at 0, and servers created on
- * the index afterwards whose max_ef falls in that class, use it.
+ * index's shape for that ef class when it beats the defaults by more than 1%
+ * (else the defaults stay): pilot_search / pilot_search_ex calls whose
+ * options leave warps_per_block or stage_rows at 0 use it, and servers
+ * created on the index afterwards whose max_ef falls in that class use its
+ * stage_rows (their step kernel keeps two warps per block).
  * (pilot_search_noalloc keeps the defaults.)
  *
  * cache_path (may be NULL): a text file of lines

@@ -373,10 +373,14 @@ pilot_status pilot_serve_create(pilot_index* index, const pilot_serve_config* co
 
     // shared-memory budget: the step kernel's per-block slice for max_ef
     S->scfg = default_search_config(X, c.max_k, c.max_ef);
-    {   // the autotuned shape of max_ef's class, if the index has one
+    {   // the autotuned staging rows of max_ef's class, if the index has them;
+        // the step kernel keeps two warps per block whatever the tuner chose
+        // for whole batches: the lanes' step kernels run side by side, and
+        // small blocks share the SMs' shared memory between them more finely
+        // (served capacity on the 1M x 96 index fell from 418k to 306k
+        // requests/s with the 8-warp blocks a batch tuning picked)
         std::lock_guard<std::mutex> lock(*static_cast<std::mutex*>(S->view.mutex));
         const TunedShape t = S->view.tuned[ef_class(int(c.max_ef))];
-        if (t.warps_per_block > 0) S->scfg.warps_per_block = std::min(t.warps_per_block, 8);
         if (t.stage_rows > 0) set_stage_rows(X, S->scfg, t.stage_rows);
     }
     int smem_max = 0;
