@@ -18,18 +18,19 @@
 //
 // Per-warp shared memory: the candidate list C (sorted 64-bit keys), the
 // query and projected query, and a staging buffer for gathered rows.  The
-// visited sets live in HBM: one open-addressing hash table per warp slot,
-// sized by ef and the degree (not by n), whose entries carry an epoch tag so
-// that a new set costs one epoch step.  An expansion probes the table for all
-// of the expanded node's neighbours at once (one 32-byte bucket per lane) and
-// gathers only the unvisited rows, each with one bulk copy into shared memory
-// completing on the warp's mbarrier.  Distances: eight lanes cover one
-// 128-byte line of a row, each lane owns up to 8 rows x its chunks, and a
-// transposing shuffle reduction leaves each row's sum in one lane.  Once C is
-// full, a plain FP32 pass with a rigorous error bound first rejects the rows
-// that cannot enter C; only the others get the exact (error-free) distance.
-// New candidates are sorted with a warp bitonic sort and merged into C by
-// rank.
+// visited sets live in HBM: one open-addressing hash table of 16-bit entries
+// per warp slot, sized by ef and the degree (not by n), whose bucket headers
+// carry an epoch tag so that a new set costs one epoch step.  An expansion
+// probes the table for all of the expanded node's neighbours at once (one
+// 32-byte bucket per lane).  In stage (1) every neighbour's reduced row is
+// copied into shared memory while the probe runs; in stages (2)(3) only the
+// unvisited full rows are copied, after it; each copy is one bulk copy
+// completing on the warp's mbarrier.  Once C is full, a plain FP32 pass with
+// a rigorous error bound first rejects the rows that cannot enter C (one row
+// per lane, or eight lanes per row for few or long rows); only the others get
+// the exact (error-free) distance, eight lanes per 128-byte line and a
+// shuffle butterfly per row.  Up to three new keys are inserted into C one at
+// a time; more are sorted with a warp bitonic sort and merged into C by rank.
 #pragma once
 
 #include <cfloat>
@@ -52,12 +53,6 @@ struct Layout {
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-__host__ __device__ inline int pow2_ceil(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
 
 // Per-warp shared memory: the fixed-size scratch arrays first, at constant
 // offsets from the warp's base (so that addressing them needs no registers of
