@@ -488,3 +488,43 @@ def test_short_results_are_padded(pilot, torch_cuda):
     ids, dists, _ = gpu_search(pilot, torch_cuda, g, np.zeros((1, 4), np.float32), 5, 8)
     assert ids[0].tolist() == [0, 1, 2, -1, -1]
     assert np.all(np.isinf(dists[0, 3:]))
+
+
+def test_large_id_space_uses_the_widest_visited_quotients(pilot, torch_cuda):
+    """Visited entries store a node's quotient within its bucket (at most 13
+    bits) rather than its id, so an index whose ids need 23 bits gets tables
+    of at least 2^14 words (1,024 buckets).  On a 4.2M-node index (a ring of
+    16 seeded random offsets, random 32-d rows, every node sampled), a search
+    whose table is capped at that floor uses 13-bit quotients, the widest the
+    encoding allows, and must still return the oracle's ids, distances and
+    counters with no insertion left without room; a cap below the floor is
+    rejected."""
+    rng = np.random.default_rng(23)
+    n, d, R = (1 << 22) + 4096, 32, 16
+    offsets = rng.choice(np.arange(1, n, dtype=np.int64), size=R, replace=False)
+    graph = ((np.arange(n, dtype=np.int64)[:, None] + offsets[None, :]) % n).astype(np.int32)
+    full = rng.standard_normal((n, d), dtype=np.float32)
+    mask = np.ones(n, np.uint8)
+    basis = np.eye(d, dtype=np.float64)
+    entries = np.arange(256, dtype=np.int32)
+    Q = rng.standard_normal((8, d), dtype=np.float32)
+    g = pilot.pilot_index_load(graph, mask, graph, basis, full, full, entries)
+    oi = oracle.OracleIndex(graph, mask, graph, basis, full, oracle.DTYPE_F32, None, full, entries, 0)
+    ref = oracle.search(oi, Q, 10, 64)
+    floor_words = 1 << (23 - 9)
+    for cap in (0, floor_words):
+        o = pilot.pilot_search_options_default()
+        o.visited_entries = cap
+        status = np.zeros(8, np.int32)
+        o.status_words = status.ctypes.data
+        cnt = np.empty((len(Q), 8), np.int32)
+        ids, dists = pilot.pilot_search_ex(g, Q, 10, 64, options=o, counters=cnt)
+        assert np.array_equal(ids, ref["ids"]) and np.array_equal(dists, ref["dists"]), cap
+        assert np.array_equal(cnt, ref["counters"]), cap
+        assert status[7] == 0, cap
+    with pytest.raises(pilot.PilotError) as e:
+        o = pilot.pilot_search_options_default()
+        o.visited_entries = floor_words // 2
+        pilot.pilot_search_ex(g, Q, 10, 64, options=o)
+    assert e.value.status == pilot.PILOT_EINVAL
+    g.free()
