@@ -333,7 +333,7 @@ void pilot_serve_destroy(pilot_server* server);
  * stage3, use_fes; NULL = the defaults; its other fields are ignored), for
  * every pair of
  *   warps_per_block  in {1, 2, 4, 8}   (queries per block; one warp each)
- *   stage_rows       in {8, 12, 16, 20, 24, 32} (rows staged per gather pass)
+ *   stage_rows       in {4, 8, 12, 16, 20, 24, 32} (rows staged per gather pass)
  * whose shared memory fits, and for the defaults.  The fastest becomes the
  * index's shape for that ef class when it beats the defaults by more than 1%
  * (else the defaults stay): pilot_search / pilot_search_ex calls whose

@@ -149,7 +149,7 @@ extern "C" pilot_status pilot_autotune(pilot_index* index, const float* queries,
     std::vector<Timed> timed;
     if (ps == PILOT_OK && def_ms < 0.0f) ps = tune_fail(PILOT_EINVAL, "the default shape does not fit this ef");
     for (int wpb : {1, 2, 4, 8}) {
-        for (int rows : {8, 12, 16, 20, 24, 32}) {
+        for (int rows : {4, 8, 12, 16, 20, 24, 32}) {
             if (ps != PILOT_OK) break;
             float ms = 0.0f;
             ps = time_shape(wpb, rows, &ms);

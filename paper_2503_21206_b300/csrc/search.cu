@@ -45,11 +45,14 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     cfg.warps_per_block = 2;
     // 24 rows of the widest kind per gather pass (an expansion probes its
     // neighbours first and gathers only the unvisited ones, typically fewer
-    // than 24 of 32), at most ~16.5 KB, at least 4 wide or 32 reduced rows
+    // than 24 of 32), at most ~16.5 KB, in whole groups of 4 rows (the
+    // pre-filter's eight-lanes-per-row layout takes 4 rows at a time), at
+    // least 4 wide or 32 reduced rows
     const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
-    int stage = 4 * (fs > rs ? fs : rs);
-    const int full24 = 24 * fs < 16896 ? 24 * fs : 16896;
-    stage = stage > full24 ? stage : full24;
+    int full_rows = 16896 / fs;
+    full_rows = full_rows > 24 ? 24 : (full_rows & ~3);
+    if (full_rows < 4) full_rows = 4;
+    const int stage = full_rows * (fs > rs ? fs : rs);
     cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
     cfg.filter = 1;
     set_visited_size(ix, cfg, ix.vis_stride);

@@ -37,7 +37,7 @@ def test_tuned_shape_keeps_results(env):
     g = pilot.load_index_data(idx)
     r = pilot.pilot_autotune(g, Q, 10, 64)
     assert r["from_cache"] == 0 and r["candidates"] >= 1
-    assert 1 <= r["warps_per_block"] <= 8 and r["stage_rows"] in (0, 8, 12, 16, 20, 24, 32)
+    assert 1 <= r["warps_per_block"] <= 8 and r["stage_rows"] in (0, 4, 8, 12, 16, 20, 24, 32)
     assert 0 < r["best_ms"] <= r["default_ms"]
     ref = _oracle(idx, Q, 10, 64)
     ids, d = pilot.pilot_search(g, Q, 10, 64)
