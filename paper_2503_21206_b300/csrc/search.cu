@@ -47,13 +47,16 @@ SearchConfig default_search_config(const DevIndex& ix, int k, int ef) {
     // neighbours first and gathers only the unvisited ones, typically fewer
     // than 24 of 32), at most ~16.5 KB, in whole groups of 4 rows (the
     // pre-filter's eight-lanes-per-row layout takes 4 rows at a time), at
-    // least 4 wide or 32 reduced rows
+    // least 4 rows
     const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
     int full_rows = 16896 / fs;
     full_rows = full_rows > 24 ? 24 : (full_rows & ~3);
     if (full_rows < 4) full_rows = 4;
     const int stage = full_rows * (fs > rs ? fs : rs);
-    cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
+    // stage (1) copies all 32 neighbours' reduced rows during the probe when
+    // they fit in this buffer; wider reduced rows are gathered after the
+    // probe, like full rows, rather than enlarge it and cost occupancy
+    cfg.stage_bytes = stage;
     cfg.filter = 1;
     set_visited_size(ix, cfg, ix.vis_stride);
     return cfg;
@@ -70,7 +73,7 @@ void set_stage_rows(const DevIndex& ix, SearchConfig& cfg, int rows) {
     rows = rows < 4 ? 4 : (rows > 32 ? 32 : rows & ~3);
     const int fs = stage_stride(ix.full_row_bytes), rs = stage_stride(ix.red_row_bytes);
     int stage = rows * (fs > rs ? fs : rs);
-    cfg.stage_bytes = stage > 32 * rs ? stage : 32 * rs;
+    cfg.stage_bytes = stage;
 }
 
 cudaError_t launch_search(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st,

@@ -794,7 +794,9 @@ __device__ __forceinline__ void new_visited_set(Warp& w, int64_t stride, uint32_
     __syncwarp();
 }
 
-template <int DT, int METRIC>
+// WIDE: reduced rows too wide for 32 staging slots (32 x stage_stride(red) >
+// stage_bytes); stage (1) then gathers them after the probe, like full rows.
+template <int DT, int METRIC, bool WIDE>
 struct Searcher {
     const DevIndex& ix;
     const SearchConfig& cfg;
@@ -880,7 +882,7 @@ struct Searcher {
             if (view == 2 && v >= 0) v = __ldg(ix.sub2full + v);
             PILOT_CHECK_INDEX(w, v, view == 1 ? ix.n_sub : ix.n);
             uint64_t k = kKeyEmpty, worst = kKeyEmpty;
-            if (view == 1) {
+            if (view == 1 && !WIDE) {
                 // stage (1): every neighbour's reduced row is copied into
                 // staging slot `lane` while its visited bucket is probed, so
                 // that the two round trips overlap; the rows of neighbours
@@ -930,8 +932,13 @@ struct Searcher {
                 const uint32_t wbits = uint32_t(worst >> 32);
                 const bool filter = full && cfg.filter && wbits != orderable(INFINITY);
                 const float thr = filter ? from_orderable(wbits + 1u) : INFINITY;   // nextup(worst distance)
-                filtered_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr,
-                                         w.q, m, cfg.stage_bytes, ix.full_host != 0, filter, thr, ix.d_pad);
+                if (WIDE && view == 1)   // stage (1) with reduced rows too wide for 32 staging slots
+                    filtered_dist<DT, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.red), ix.red_row_bytes,
+                                              ix.red_scales, w.qp, m, cfg.stage_bytes, false,
+                                              filter && !(DT == 2 && METRIC == 0), thr, ix.dp_pad);
+                else
+                    filtered_dist<0, METRIC>(w, reinterpret_cast<const uint8_t*>(ix.full), ix.full_row_bytes, nullptr,
+                                             w.q, m, cfg.stage_bytes, ix.full_host != 0, filter, thr, ix.d_pad);
                 __syncwarp();
                 if (lane < m) k = make_key(w.dist()[lane], w.cand()[lane]);
             }
@@ -1225,7 +1232,7 @@ __device__ __forceinline__ Warp setup_warp(const Layout& L, uint8_t* smem, const
     return w;
 }
 
-template <int DT, int METRIC>
+template <int DT, int METRIC, bool WIDE>
 __global__ void __launch_bounds__(256, 2) search_kernel(DevIndex ix, SearchConfig cfg, SearchIO io, Layout L) {
     extern __shared__ __align__(128) uint8_t smem[];
     Warp w = setup_warp(L, smem, ix, cfg);
@@ -1235,7 +1242,7 @@ __global__ void __launch_bounds__(256, 2) search_kernel(DevIndex ix, SearchConfi
     const int slot = blockIdx.x * cfg.warps_per_block + (threadIdx.x >> 5);   // < ix.vis_slots (launch bound)
     w.vis = ix.vis + int64_t(slot) * ix.vis_stride;
     w.epoch_ctr = ix.vis_epoch[slot];
-    Searcher<DT, METRIC> s{ix, cfg, w};
+    Searcher<DT, METRIC, WIDE> s{ix, cfg, w};
     for (;;) {
         int64_t q = 0;
         if (w.lane == 0) q = atomicAdd(&io.status[1], 1);
@@ -1267,14 +1274,14 @@ __global__ void __launch_bounds__(256, 2) search_kernel(DevIndex ix, SearchConfi
 // resume from their slot, and slots already finished are skipped.  Finished
 // requests write their top-k to the host-mapped result rows, mark their slot
 // done and raise their done flag.
-template <int DT, int METRIC>
+template <int DT, int METRIC, bool WIDE>
 __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchConfig cfg, ServeIO sio, Layout L) {
     extern __shared__ __align__(128) uint8_t smem[];
     Warp w = setup_warp(L, smem, ix, cfg);
 #ifdef PILOT_CHECKED
     w.status = nullptr;
 #endif
-    Searcher<DT, METRIC> s{ix, cfg, w};
+    Searcher<DT, METRIC, WIDE> s{ix, cfg, w};
     const int n_active = *reinterpret_cast<const volatile int32_t*>(sio.n_active);
     for (;;) {
         int i = 0;
@@ -1350,8 +1357,8 @@ __global__ void __launch_bounds__(256, 2) serve_step_kernel(DevIndex ix, SearchC
     if (w.lane == 0 && ov && sio.vis_overflow) atomicAdd(sio.vis_overflow, int(ov));
 }
 
-template <int DT, int METRIC>
-cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const SearchIO& io, cudaStream_t st,
+template <int DT, int METRIC, bool WIDE>
+cudaError_t launch_k(const DevIndex& ix, const SearchConfig& cfg_in, const SearchIO& io, cudaStream_t st,
                      int num_sms) {
     const SearchConfig& cfg = cfg_in;
     const Layout L = make_layout(ix, cfg);
@@ -1360,11 +1367,11 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const Searc
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, METRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, METRIC, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, METRIC>, cfg.warps_per_block * 32,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, METRIC, WIDE>, cfg.warps_per_block * 32,
                                                       smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -1373,12 +1380,12 @@ cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const Searc
     const int64_t need = (io.nq + cfg.warps_per_block - 1) / cfg.warps_per_block;
     if (blocks > need) blocks = need;
     if (blocks < 1) return cudaSuccess;
-    search_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, io, L);
+    search_kernel<DT, METRIC, WIDE><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, io, L);
     return cudaGetLastError();
 }
 
-template <int DT, int METRIC>
-cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
+template <int DT, int METRIC, bool WIDE>
+cudaError_t serve_prepare_k(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
                             size_t* smem_out) {
     const Layout L = make_layout(ix, cfg);
     const size_t smem = size_t(L.per_warp) * cfg.warps_per_block;
@@ -1386,11 +1393,11 @@ cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > size_t(smem_max)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(serve_step_kernel<DT, METRIC>,
+    cudaError_t e = cudaFuncSetAttribute(serve_step_kernel<DT, METRIC, WIDE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_step_kernel<DT, METRIC>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_step_kernel<DT, METRIC, WIDE>,
                                                       cfg.warps_per_block * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -1401,13 +1408,39 @@ cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num
     return cudaSuccess;
 }
 
-template <int DT, int METRIC>
-cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg_in, const ServeIO& sio, cudaStream_t st,
+template <int DT, int METRIC, bool WIDE>
+cudaError_t serve_launch_k(const DevIndex& ix, const SearchConfig& cfg_in, const ServeIO& sio, cudaStream_t st,
                            int blocks, size_t smem) {
     const SearchConfig& cfg = cfg_in;
-    serve_step_kernel<DT, METRIC><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, sio,
+    serve_step_kernel<DT, METRIC, WIDE><<<unsigned(blocks), cfg.warps_per_block * 32, smem, st>>>(ix, cfg, sio,
                                                                                            make_layout(ix, cfg));
     return cudaGetLastError();
+}
+
+// Whether a configuration's reduced rows are too wide for stage (1)'s 32
+// staging slots (the kernel instance without the overlapped copies).
+__host__ __device__ inline bool wide_reduced(const DevIndex& ix, const SearchConfig& cfg) {
+    return 32 * stage_stride(ix.red_row_bytes) > cfg.stage_bytes;
+}
+
+template <int DT, int METRIC>
+cudaError_t launch_t(const DevIndex& ix, const SearchConfig& cfg, const SearchIO& io, cudaStream_t st, int num_sms) {
+    return wide_reduced(ix, cfg) ? launch_k<DT, METRIC, true>(ix, cfg, io, st, num_sms)
+                                 : launch_k<DT, METRIC, false>(ix, cfg, io, st, num_sms);
+}
+
+template <int DT, int METRIC>
+cudaError_t serve_prepare_t(const DevIndex& ix, const SearchConfig& cfg, int num_sms, int max_warps, int* blocks,
+                            size_t* smem_out) {
+    return wide_reduced(ix, cfg) ? serve_prepare_k<DT, METRIC, true>(ix, cfg, num_sms, max_warps, blocks, smem_out)
+                                 : serve_prepare_k<DT, METRIC, false>(ix, cfg, num_sms, max_warps, blocks, smem_out);
+}
+
+template <int DT, int METRIC>
+cudaError_t serve_launch_t(const DevIndex& ix, const SearchConfig& cfg, const ServeIO& sio, cudaStream_t st,
+                           int blocks, size_t smem) {
+    return wide_reduced(ix, cfg) ? serve_launch_k<DT, METRIC, true>(ix, cfg, sio, st, blocks, smem)
+                                 : serve_launch_k<DT, METRIC, false>(ix, cfg, sio, st, blocks, smem);
 }
 
 }  // namespace
